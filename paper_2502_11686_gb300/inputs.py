@@ -1,0 +1,183 @@
+"""Seeded synthetic smoothing problems (host, FP64, numpy).
+
+This module only draws inputs; it holds none of the smoother's arithmetic, so the CUDA path and
+the CPU oracle can both consume the very same bytes.  Layout of a :class:`Problem`
+(row-major, step-major):
+
+* ``F, H, K``: ``[k-1, n, n]`` -- evolution equation i links state i to state i+1,
+  ``H_i u_{i+1} = F_i u_i + c_i + eps_i`` with ``cov(eps_i) = K_i``;
+* ``c``: ``[k-1, n]`` or ``None`` (all zero);
+* ``m``: int32 ``[k]`` observation counts (0 allowed);
+* ``G``: packed, observation i occupies ``m_i * n`` values (``o_i = G_i u_i + delta_i``);
+* ``o``: packed ``sum(m_i)`` values;
+* ``C``: packed, observation i occupies ``m_i * m_i`` values (``cov(delta_i) = C_i``).
+
+Recipes (the paper's own benchmark problems are synthetic, Section 5: orthonormal F, H = I,
+random observations):
+
+* :func:`cv_problem` -- 2-D constant velocity, n=4, m=2, G ~ N(0,1), K=0.01 I, C=0.25 I,
+  trajectory and observations simulated from the seed.
+* :func:`random_problem` -- F = scale * (random orthogonal), one draw per problem stored for
+  every step; H = I; G_i ~ N(0, 1/n) (variance 1/n) drawn per step; K_i, C_i = L L^T per step
+  with L lower triangular, diagonal U[0.5, 1.5], off-diagonal N(0, 0.1^2) (std 0.1); c = 0;
+  o ~ N(0, 1).
+* :func:`scalar_random_walk` -- n = m = 1, F = H = G = 1, K = q, C = r.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Problem:
+    k: int
+    n: int
+    m: np.ndarray
+    F: np.ndarray
+    H: np.ndarray
+    c: np.ndarray | None
+    K: np.ndarray
+    G: np.ndarray
+    o: np.ndarray
+    C: np.ndarray
+    truth: np.ndarray | None = None
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def steps(self) -> int:
+        return self.k
+
+    def input_bytes(self) -> int:
+        arrs = [self.m, self.F, self.H, self.K, self.G, self.o, self.C]
+        if self.c is not None:
+            arrs.append(self.c)
+        return int(sum(a.nbytes for a in arrs))
+
+    def obs_offsets(self):
+        """Packed offsets (G/o offset in rows, C offset in values) of every observation."""
+        m = self.m.astype(np.int64)
+        go = np.zeros(self.k + 1, dtype=np.int64)
+        co = np.zeros(self.k + 1, dtype=np.int64)
+        np.cumsum(m, out=go[1:])
+        np.cumsum(m * m, out=co[1:])
+        return go, co
+
+
+def _spd_factor(rng, count, d, off_std=0.1):
+    """Lower-triangular L with diagonal U[0.5,1.5] and off-diagonal N(0, off_std^2)."""
+    L = np.tril(rng.normal(0.0, off_std, size=(count, d, d)), -1)
+    idx = np.arange(d)
+    L[:, idx, idx] = rng.uniform(0.5, 1.5, size=(count, d))
+    return L
+
+
+def random_spd(rng, count, d, off_std=0.1):
+    L = _spd_factor(rng, count, d, off_std)
+    return np.matmul(L, np.swapaxes(L, 1, 2))
+
+
+def random_orthogonal(rng, n):
+    q, r = np.linalg.qr(rng.normal(size=(n, n)))
+    return q * np.sign(np.diag(r))[None, :]
+
+
+def cv_problem(k: int = 1000, seed: int = 0, dt: float = 0.1, m: int = 2) -> Problem:
+    """2-D constant-velocity model: u = (position, velocity), F = [[I, dt I], [0, I]]."""
+    rng = np.random.default_rng(seed)
+    n = 4
+    I2 = np.eye(2)
+    F1 = np.block([[I2, dt * I2], [np.zeros((2, 2)), I2]])
+    Kc, Cc = 0.01, 0.25
+    truth = np.zeros((k, n))
+    truth[0] = rng.normal(size=n)
+    for i in range(1, k):
+        truth[i] = F1 @ truth[i - 1] + rng.normal(0.0, np.sqrt(Kc), size=n)
+    G = rng.normal(size=(k, m, n))
+    o = np.einsum("kij,kj->ki", G, truth) + rng.normal(0.0, np.sqrt(Cc), size=(k, m))
+    return Problem(
+        k=k, n=n, m=np.full(k, m, dtype=np.int32),
+        F=np.ascontiguousarray(np.broadcast_to(F1, (k - 1, n, n))),
+        H=np.ascontiguousarray(np.broadcast_to(np.eye(n), (k - 1, n, n))),
+        c=None,
+        K=np.ascontiguousarray(np.broadcast_to(Kc * np.eye(n), (k - 1, n, n))),
+        G=G.reshape(-1), o=o.reshape(-1),
+        C=np.ascontiguousarray(np.broadcast_to(Cc * np.eye(m), (k, m, m))).reshape(-1),
+        truth=truth, name=f"cv k={k} n=4 m={m}")
+
+
+def random_problem(k: int, n: int, m=None, seed: int = 0, f_scale: float = 0.99,
+                   with_c: bool = False, g_var=None) -> Problem:
+    """Random orthogonal dynamics (scaled), H = I, G_i ~ N(0, 1/n), SPD K_i and C_i per step.
+
+    ``m`` is an int (uniform) or an int array of length k (0 allowed).
+    """
+    rng = np.random.default_rng(seed)
+    m_arr = np.full(k, n if m is None else m, dtype=np.int32) if np.isscalar(m) or m is None \
+        else np.asarray(m, dtype=np.int32)
+    assert m_arr.shape == (k,)
+    F1 = f_scale * random_orthogonal(rng, n)
+    F = np.ascontiguousarray(np.broadcast_to(F1, (max(k - 1, 0), n, n)))
+    H = np.ascontiguousarray(np.broadcast_to(np.eye(n), (max(k - 1, 0), n, n)))
+    K = random_spd(rng, max(k - 1, 0), n)
+    gstd = np.sqrt(1.0 / n if g_var is None else g_var)
+    tot = int(m_arr.sum())
+    G = rng.normal(0.0, gstd, size=tot * n)
+    o = rng.normal(size=tot)
+    if np.all(m_arr == m_arr[0]):
+        mm = int(m_arr[0])
+        C = random_spd(rng, k, mm).reshape(-1) if mm > 0 else np.zeros(0)
+    else:
+        C = np.concatenate([random_spd(rng, 1, int(mi)).reshape(-1) if mi > 0 else np.zeros(0)
+                            for mi in m_arr]) if tot else np.zeros(0)
+    c = rng.normal(size=(k - 1, n)) if with_c else None
+    return Problem(k=k, n=n, m=m_arr, F=F, H=H, c=c, K=K, G=G, o=o, C=C,
+                   name=f"random k={k} n={n} m={m if np.isscalar(m) or m is None else 'var'}")
+
+
+def consistent_problem(k: int, n: int, m, seed: int = 0, f_scale: float = 0.99,
+                       with_c: bool = True) -> Problem:
+    """Noise-free data: o_i = G_i u_i and u_{i+1} = H^{-1}(F_i u_i + c_i) exactly (H = I), so
+    the minimiser is the generating trajectory and the minimal objective is 0."""
+    p = random_problem(k, n, m, seed=seed, f_scale=f_scale, with_c=with_c)
+    rng = np.random.default_rng(seed + 7919)
+    u = np.zeros((k, n))
+    u[0] = rng.normal(size=n)
+    for i in range(1, k):
+        u[i] = p.F[i - 1] @ u[i - 1] + (p.c[i - 1] if p.c is not None else 0.0)
+    go, _ = p.obs_offsets()
+    o = np.zeros_like(p.o)
+    for i in range(k):
+        mi = int(p.m[i])
+        if mi:
+            o[go[i]:go[i] + mi] = p.G[go[i] * n:(go[i] + mi) * n].reshape(mi, n) @ u[i]
+    p.o = o
+    p.truth = u
+    p.name = f"consistent k={k} n={n}"
+    return p
+
+
+def scalar_random_walk(k: int, q: float, r: float, seed: int = 0) -> Problem:
+    rng = np.random.default_rng(seed)
+    x = np.cumsum(rng.normal(0.0, np.sqrt(q), size=k))
+    o = x + rng.normal(0.0, np.sqrt(r), size=k)
+    return Problem(k=k, n=1, m=np.ones(k, dtype=np.int32),
+                   F=np.ones((k - 1, 1, 1)), H=np.ones((k - 1, 1, 1)), c=None,
+                   K=np.full((k - 1, 1, 1), q), G=np.ones(k), o=o, C=np.full(k, r),
+                   truth=x, name=f"random walk q={q} r={r}")
+
+
+def uneven_batch(nprob: int = 512, seed0: int = 0, k_lo: int = 100, k_hi: int = 20000,
+                 ns=(4, 8, 16, 32)):
+    """Independent problems, problem i drawn from seed seed0+i: k log-uniform in [k_lo, k_hi],
+    n uniform over ``ns``, m = n/2 or n (equally likely)."""
+    probs = []
+    for i in range(nprob):
+        rng = np.random.default_rng(seed0 + i)
+        k = int(round(np.exp(rng.uniform(np.log(k_lo), np.log(k_hi)))))
+        n = int(rng.choice(ns))
+        m = n if rng.uniform() < 0.5 else n // 2
+        probs.append(random_problem(k, n, m, seed=seed0 + i, f_scale=0.99))
+    return probs
