@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput of the odd-even Kalman smoother on GB300: smoothed steps per second.
+
+One step of the benchmark is one pass of the whole path over one synthetic problem already
+resident in HBM: whitening, the odd-even QR factorization (all levels), back substitution and
+the odd-even SelInv covariances of every state, all through the C ABI (libks.so).
+
+Default workload: k = 1,000,000 states, n = m = 6, F = 0.99 * random orthogonal, H = I,
+G_i ~ N(0, 1/6), K_i, C_i = L L^T (L lower triangular, diagonal U[0.5, 1.5], off-diagonal std
+0.1), FP64.  Its inputs (1.5 GB) are larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank smooths its own problem (seed = rank):
+the method has no exchange step between independent problems, so N GPUs are N replicas.
+``--impl reference`` times the CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "smoothed steps/s (FP64 plain vs FP32+refine batched) on 1 GB300; % roofline; p99 ms"
+UNIT = "steps/s"
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 peak is provided)
+FP32_PEAK_TFLOPS = 80.5      # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+
+WORKLOADS = {
+    "long_k1e6_n6": dict(k=1_000_000, n=6, m=6, f_scale=0.99, sample_k=1_000_000,
+                         desc="k=1,000,000 states, n=m=6, F=0.99*orth, H=I, G~N(0,1/6), "
+                              "K,C=LL^T per step; states + all covariances"),
+    "cv_k1000_n4": dict(k=1000, n=4, m=2, cv=True, sample_k=1000,
+                        desc="k=1000, 2-D constant velocity n=4, m=2, G~N(0,1), K=0.01I, "
+                             "C=0.25I; states + all covariances"),
+    "dense_k1e5_n48": dict(k=100_000, n=48, m=48, f_scale=0.995, sample_k=1500,
+                           desc="k=100,000 states, n=m=48, F=0.995*orth, H=I, G~N(0,1/48), "
+                                "K,C=LL^T per step; states + all covariances"),
+}
+
+
+def make_problem(wl, seed, k=None):
+    from paper_2502_11686_gb300 import inputs
+    k = k or wl["k"]
+    if wl.get("cv"):
+        return inputs.cv_problem(k=k, seed=seed)
+    return inputs.random_problem(k, wl["n"], wl["m"], seed=seed, f_scale=wl["f_scale"])
+
+
+def flops_per_step(n, m, precision):
+    """Algorithmic flops per smoothed step of each phase (the structured Householder scheme:
+    a reflector touches the p+1 rows of one triangular-over-full pair)."""
+    def tpqrt(p, comps):  # n reflectors, each applied to the trailing factor columns + comps
+        return 2 * p * n * (n - 1) + 4 * p * n * comps
+    whiten = (n ** 3 + m ** 3) / 3 + n * n * (2 * n + 1) + m * m * (n + 1) + tpqrt(m, 1)
+    level = tpqrt(n, n + 1) + tpqrt(n, 2 * n + 1) + tpqrt(n, 1)
+    backsub = 5 * n * n
+    selinv = 3 * n ** 3 + 8 * n ** 3 + 6 * n ** 3
+    refine = (4 * n * n + 2 * n * n) + (2 * n * m + m * m * 2 + 2 * n * m) + 5 * n * n + 5 * n * n \
+        if precision == "fp32_refine" else 0
+    return {"whiten": whiten, "level": level, "backsub": backsub, "selinv": selinv,
+            "refine": refine}
+
+
+def bytes_per_step(n, m, precision):
+    """Algorithmic HBM bytes per smoothed step of each phase (each array read or written once)."""
+    t = 4 if precision == "fp32_refine" else 8
+    rec = (3 * n * n + 2 * n) * t           # level-buffer record
+    rrec = (3 * n * n + n) * t              # R-store record
+    inputs = (3 * n * n + m * n + m * m + m) * 8
+    return {"whiten": inputs + rec + (8 * (n * n + m * m) if t == 4 else 0),
+            "level": 2 * rec + rrec,        # read the level (2 columns -> 1), write R row
+            "backsub": rrec + 3 * n * 8,
+            "selinv": rrec + 3 * n * n * 8 + 2 * n * n * t + n * n * 8,
+            "refine": (inputs + 8 * (n * n + m * m) + 10 * n * 8) if t == 4 else 0}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock, power and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        pw = [float(r[3]) for r in self.rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def oracle_rate(wl, budget_s=10.0):
+    """Steps/s of the CPU oracle (1 host core) on a bounded sample of the workload."""
+    import oracle
+    p = make_problem(wl, seed=0, k=wl["sample_k"])
+    oracle.smooth(p)  # load + warm
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.smooth(p, covariances=True)
+        steps += p.k
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    sample = (f"{wl['sample_k']} states of the same recipe (n={wl['n']}, m={wl['m']}), states + "
+              f"covariances, repeated for {el:.1f} s")
+    return steps / el, sample
+
+
+def reference_arm(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    p = make_problem(wl, seed=0, k=wl["sample_k"])
+    oracle.smooth(p)
+    for _ in range(args.warmup):
+        oracle.smooth(p, covariances=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.smooth(p, covariances=True)
+    el = time.perf_counter() - t0
+    value = p.k * args.steps / el
+    sample = f"{p.k} states of the {args.workload} recipe per step, states + covariances"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl['desc']}", "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="long_k1e6_n6", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_refine"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args, wl)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2502_11686_gb300 import native, problem_arrays
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    p = make_problem(wl, seed=rank)
+    k, n = p.k, p.n
+    m = int(p.m[0])
+    arr = problem_arrays(p, f"cuda:{local}")
+    stream = torch.cuda.Stream()
+    opts = native.ks_default_options()
+    opts.device = local
+    opts.precision = native.KS_FP64 if args.precision == "fp64" else native.KS_FP32_REFINE
+    opts.stream = stream.cuda_stream
+    opts.sync = 0
+    opts.profile = 1
+    ctx = native.ks_create(opts)
+    u = torch.empty((k, n), dtype=torch.float64, device=f"cuda:{local}")
+    cov = torch.empty((k, n, n), dtype=torch.float64, device=f"cuda:{local}")
+    h = None
+
+    def step(a, uo, co):
+        nonlocal h
+        _, h, _ = native.ks_smooth(ctx, k, n, a["m"], a["F"], a["H"], a["c"], a["K"], a["G"],
+                                   a["o"], a["C"], uo, keep=True, reuse=h)
+        native.ks_covariances(ctx, h, co)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(arr, u, cov)
+    st, info = native.ks_sync(ctx)
+    if st != native.KS_OK:
+        raise native.KsError(st, native.ks_last_error(ctx), info)
+    native.ks_profile_read(ctx, reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                step(arr, u, cov)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    st, info = native.ks_sync(ctx)
+    if st != native.KS_OK:
+        raise native.KsError(st, native.ks_last_error(ctx), info)
+    ms = ev0.elapsed_time(ev1)
+    prof = native.ks_profile_read(ctx, reset=True)
+    t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * k * args.steps / (ms_max / 1e3)
+
+    # End to end through the same C ABI with pinned host buffers: every step copies its
+    # inputs in and its states and covariances out inside the timed region.
+    e2e = None
+    if not args.no_e2e:
+        harr = {nm: (torch.from_numpy(np.ascontiguousarray(getattr(p, nm))).pin_memory()
+                     if getattr(p, nm) is not None and nm != "m" else getattr(p, nm))
+                for nm in ("m", "F", "H", "c", "K", "G", "o", "C")}
+        hu = torch.empty((k, n), dtype=torch.float64).pin_memory()
+        hc = torch.empty((k, n, n), dtype=torch.float64).pin_memory()
+        e_steps = max(3, min(args.steps, 10))
+        with torch.cuda.stream(stream):
+            step(harr, hu, hc)
+            native.ks_sync(ctx)
+            barrier()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(e_steps):
+                step(harr, hu, hc)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        st, info = native.ks_sync(ctx)
+        if st != native.KS_OK:
+            raise native.KsError(st, native.ks_last_error(ctx), info)
+        e_ms = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device=f"cuda:{local}")
+        if world > 1:
+            dist.all_reduce(e_ms, op=dist.ReduceOp.MAX)
+        in_bytes = sum(int(v.numel() * v.element_size()) for nm, v in harr.items()
+                       if v is not None and nm != "m") + int(p.m.nbytes)
+        e2e = {"value": world * k * e_steps / (float(e_ms.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": in_bytes,
+               "d2h_bytes_per_step": int(hu.numel() * 8 + hc.numel() * 8),
+               "steps": e_steps}
+        native.ks_profile_read(ctx, reset=True)
+
+    if h is not None:
+        native.ks_release(ctx, h)
+    native.ks_destroy(ctx)
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    fl = flops_per_step(n, m, args.precision)
+    by = bytes_per_step(n, m, args.precision)
+    phase_ms = {ph: v / args.steps for ph, v in prof["phase_ms"].items() if v > 0}
+    top = max(("whiten", "level", "backsub", "selinv", "refine"), key=lambda ph: phase_ms.get(ph, 0))
+    peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
+    achieved = fl[top] * k / (phase_ms[top] / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": f"{top} phase", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": ("nominal FP64 rate of the GB300 (1.25 TFLOP/s), no measured FP64 peak"
+                            if args.precision == "fp64" else
+                            "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
+            "flops_per_step": fl[top], "hbm_bytes_per_step": by[top],
+            "achieved_hbm_gbs": by[top] * k / (phase_ms[top] / 1e3) / 1e9,
+            "traffic": None}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, sample = oracle_rate(wl)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak = peaks.get("hbm_gbs")
+    except (OSError, ValueError):
+        hbm_peak = 6800.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {wl['desc']}", "k": k, "n": n, "m": m,
+                   "precision": args.precision,
+                   "l2": f"inputs ({p.input_bytes() / 1e9:.2f} GB) larger than L2 (129 MB), no flush",
+                   "parallelism": "replicas only (one independent problem per GPU)"},
+        "roofline": roof,
+        "hbm_frac_of_measured": roof["achieved_hbm_gbs"] / hbm_peak if hbm_peak else None,
+        "phase_ms_per_step": phase_ms,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": prof["launches"],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

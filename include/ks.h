@@ -1,0 +1,163 @@
+/*
+ * ks.h -- C ABI of the GB300 odd-even Kalman smoother (libks.so).
+ *
+ * Method: Gargir & Toledo, "Parallel-in-Time Kalman Smoothing Using Orthogonal
+ * Transformations" (IPDPS 2025).  The smoother solves the generalized least-squares problem of
+ * Section 2 (eq. of the generalized least-squares estimator)
+ *
+ *     u_hat = argmin_u  sum_i || V_i (H_i u_{i+1} - F_i u_i - c_i) ||^2
+ *                     + sum_i || W_i (o_i - G_i u_i) ||^2,     V_i^T V_i = K_i^{-1},
+ *                                                               W_i^T W_i = C_i^{-1},
+ *
+ * by the odd-even block QR factorization of Section 3 (Householder QR of pairs of block rows,
+ * even block columns eliminated first, recursion on the odd ones), back substitution through
+ * the same recursion (Section 3.1), and the covariances cov(u_hat_i) -- the diagonal blocks of
+ * (R^T R)^{-1} -- by the odd-even block SelInv of Section 4 (Algorithm 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - k is the NUMBER OF STATES u_0..u_{k-1} (the paper numbers them 0..k, so its k is ours
+ *    minus one).  Evolution equation i (0 <= i < k-1) links u_i to u_{i+1}:
+ *    H_i u_{i+1} = F_i u_i + c_i + eps_i, cov(eps_i) = K_i.  It is the paper's equation i+1.
+ *  - Observation i: o_i = G_i u_i + delta_i with m_i rows (0 allowed), cov(delta_i) = C_i.
+ *    C_i is the paper's L_i.  There is no prior on u_0 (the paper's unknown initial state).
+ *  - All matrices are FP64, row-major, step-major:
+ *      F, H, K : [k-1][n][n]        c : [k-1][n]  (NULL means c = 0)
+ *      G : packed, observation i occupies m_i*n values, in step order
+ *      o : packed, sum(m_i) values
+ *      C : packed, observation i occupies m_i*m_i values (SPD)
+ *      u_out : [k][n]               cov_out : [k][n][n]
+ *  - Every array pointer may be a DEVICE pointer (e.g. torch.Tensor.data_ptr() on the ctx's
+ *    device) or a HOST pointer (pageable or pinned); the library detects which with
+ *    cudaPointerGetAttributes and stages host arrays through its own device buffers on the
+ *    ctx's stream.  `m` is always a host array.  The caller keeps ownership of every array.
+ *  - Calls are ordered on the ctx's stream.  With ks_options.sync = 1 (the default) every
+ *    call returns after its work is complete and reports device-detected errors; with
+ *    sync = 0 calls return after enqueueing and ks_sync() reports errors.
+ *  - No call throws.  On failure the return value says why, *info (when given) holds the
+ *    first failing step / column, and ks_last_error() a message.  Outputs are undefined
+ *    unless the call returned KS_OK.
+ *  - One ks_ctx must not be used from two host threads at the same time.
+ */
+#ifndef KS_H
+#define KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ks_ctx ks_ctx;
+typedef struct ks_fac ks_fac;
+typedef ks_fac *ks_handle;
+
+typedef enum {
+    KS_OK = 0,
+    KS_ERR_ARG = 1,        /* bad size, NULL pointer, unsupported n for this precision */
+    KS_ERR_NOT_SPD = 2,    /* a K_i or C_i has no Cholesky factor; info = step i */
+    KS_ERR_SINGULAR = 3,   /* a diagonal block of R is singular or not finite (the states are
+                              not determined by the data); info = state index */
+    KS_ERR_OOM = 4,        /* device allocation failed */
+    KS_ERR_CUDA = 5,       /* a CUDA runtime call failed; see ks_last_error */
+    KS_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    KS_ERR_NO_FACTOR = 7   /* the handle holds no factorization */
+} ks_status;
+
+typedef enum {
+    KS_FP64 = 0,         /* every step of the method in FP64 */
+    KS_FP32_REFINE = 1   /* FP64 Cholesky factors of K_i, C_i; whitened blocks, Householder QR,
+                            back substitution and SelInv in FP32; then one FP64 iterative-
+                            refinement step of the states (FP64 residual of the least-squares
+                            system, corrected semi-normal equations with the FP32 R) */
+} ks_precision;
+
+typedef struct {
+    int device;         /* CUDA device ordinal */
+    int precision;      /* ks_precision */
+    void *stream;       /* cudaStream_t to run on; NULL = a stream owned by the ctx */
+    size_t mem_budget;  /* bytes of device work memory the ctx may hold; 0 = no limit */
+    int sync;           /* 1 = each call waits for its work and reports device errors */
+    int profile;        /* 1 = time every phase with CUDA events on the ctx's stream */
+} ks_options;
+
+/* Phases reported by ks_profile_read (indices of phase_ms / phase_launches). */
+typedef enum {
+    KS_PHASE_WHITEN = 0,   /* Cholesky factors, whitened blocks, observation pre-reduction */
+    KS_PHASE_LEVEL = 1,    /* the odd-even levels of the QR factorization (all levels) */
+    KS_PHASE_BACKSUB = 2,  /* base block and back substitution (all levels) */
+    KS_PHASE_REFINE = 3,   /* FP64 residual, R^T w = g, R d = w, u += d */
+    KS_PHASE_SELINV = 4,   /* odd-even SelInv (all levels) and the lag-one gather */
+    KS_PHASE_COPY = 5,     /* staging of host arrays in and out */
+    KS_NPHASES = 6
+} ks_phase;
+
+typedef struct {
+    uint64_t launches;                  /* kernels this ctx launched */
+    uint64_t phase_launches[KS_NPHASES];
+    double phase_ms[KS_NPHASES];        /* GPU time per phase (profile = 1 only) */
+    uint64_t calls;                     /* ks_smooth + ks_covariances calls */
+} ks_profile;
+
+/* Fills *opt with the defaults: device 0, KS_FP64, ctx-owned stream, no budget, sync = 1,
+ * profile = 0. */
+void ks_default_options(ks_options *opt);
+
+/* Creates a context.  opt may be NULL (defaults).  Returns KS_OK, KS_ERR_ARG or KS_ERR_CUDA. */
+ks_status ks_create(ks_ctx **out, const ks_options *opt);
+
+/*
+ * Smoothed states (Section 3: factorization, transformation of the right-hand side and back
+ * substitution).  Arrays as in the header comment; u_out receives [k][n] FP64.
+ * keep: NULL, or receives a handle that retains the factorization for ks_covariances; the
+ *       handle owns device memory until ks_release or ks_destroy.  If *keep already holds a
+ *       live handle of this ctx with the same k, n and precision, its memory is reused (no
+ *       allocation) and the same handle is returned; any other non-NULL *keep is ignored.
+ * info: NULL, or receives the first failing step / state index (-1 if none).
+ * n must satisfy 1 <= n <= ks_max_n(ctx) and every m_i <= ks_max_m(ctx, n).
+ */
+ks_status ks_smooth(ks_ctx *ctx, int64_t k, int n, const int32_t *m,
+                    const double *F, const double *H, const double *c, const double *K,
+                    const double *G, const double *o, const double *C,
+                    double *u_out, ks_handle *keep, int64_t *info);
+
+/*
+ * Covariances of the smoothed states, cov(u_hat_i) = [(R^T R)^{-1}]_{ii}, by the odd-even
+ * block SelInv (Section 4, Algorithm 2) on the factorization held by `h`.
+ * cov_out: [k][n][n] FP64 (host or device).  cross_out: NULL, or [k-1][n][n] FP64 receiving
+ * the lag-one blocks cov(u_hat_i, u_hat_{i+1}), which Algorithm 2 computes along the way.
+ */
+ks_status ks_covariances(ks_ctx *ctx, ks_handle h, double *cov_out, double *cross_out);
+
+/* Minimal value of the objective (the squared norm of the rows that the factorization
+ * discards), FP64, for the factorization held by `h`.  Written to *out (host). */
+ks_status ks_residual(ks_ctx *ctx, ks_handle h, double *out);
+
+/* Frees a handle's device memory.  NULL is a no-op. */
+ks_status ks_release(ks_ctx *ctx, ks_handle h);
+
+/* Waits for the ctx's stream and reports the first device-detected error since the last
+ * report (for sync = 0). */
+ks_status ks_sync(ks_ctx *ctx, int64_t *info);
+
+/* Frees every handle and buffer of the context.  NULL is a no-op. */
+ks_status ks_destroy(ks_ctx *ctx);
+
+/* Message of the last failure on ctx (never NULL; "" if none). */
+const char *ks_last_error(const ks_ctx *ctx);
+
+/* Counters of the ctx since its creation or the last reset (reset != 0 zeroes them after the
+ * read).  Waits for the ctx's stream so that the phase times are complete. */
+ks_status ks_profile_read(ks_ctx *ctx, ks_profile *out, int reset);
+
+/* Largest state dimension n this ctx's precision supports on its device. */
+int ks_max_n(const ks_ctx *ctx);
+
+/* Largest per-step observation count m_i supported for state dimension n. */
+int ks_max_m(const ks_ctx *ctx, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KS_H */

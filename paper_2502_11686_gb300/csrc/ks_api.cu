@@ -1,0 +1,591 @@
+// ks_api.cu -- the C ABI declared in include/ks.h: argument checks, device work memory, staging
+// of host arrays, and the launch sequence of one smoothing call:
+//   whitening -> level 0 .. L-1 of the odd-even factorization -> base -> back substitution
+//   (levels L .. 0) [-> FP64 refinement in KS_FP32_REFINE mode] -> copy-out -> status.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/ks.h"
+#include "ks_internal.cuh"
+
+using namespace ks;
+
+struct ks_fac {
+    int64_t k = 0;
+    int n = 0;
+    int precision = 0;
+    void* R = nullptr;        // R store, k records of 3n^2+n elements (T)
+    double* resid = nullptr;  // [2k]: residual parts of the level tiles and of the whitening
+};
+
+struct ks_ctx {
+    int device = 0;
+    int precision = KS_FP64;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+    int sync = 1;
+    std::string err;
+    unsigned long long* d_bad = nullptr;
+    unsigned long long* h_bad = nullptr;  // pinned
+    double* h_scalar = nullptr;           // pinned
+    void* ws = nullptr;
+    size_t ws_size = 0;
+    std::set<ks_fac*> facs;
+    int smem_optin = 0;
+    int profile = 0;
+    ks_profile prof{};
+    struct Pending { int phase; cudaEvent_t a, b; };
+    std::vector<Pending> pending;     // recorded phase events not yet read
+    std::vector<cudaEvent_t> spare;   // event pool
+};
+
+namespace {
+
+constexpr int KS_NMAX_API = 64;
+
+ks_status fail(ks_ctx* ctx, ks_status s, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return s;
+}
+
+#define KS_CUDA(ctx, call)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? KS_ERR_OOM : KS_ERR_CUDA,  \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                   \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (p == nullptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Bump allocator over the ctx workspace (256-byte aligned pieces).
+struct Plan {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off += (bytes + 255) & ~size_t(255);
+        return o;
+    }
+};
+
+ks_status reserve(ks_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_size) return KS_OK;
+    if (ctx->budget && bytes > ctx->budget)
+        return fail(ctx, KS_ERR_OOM, "work memory %zu bytes exceeds the ctx budget %zu", bytes, ctx->budget);
+    KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_size = 0;
+    KS_CUDA(ctx, cudaMalloc(&ctx->ws, bytes));
+    ctx->ws_size = bytes;
+    return KS_OK;
+}
+
+int tile_smem_bytes(int n, bool fp32) { return tile_layout(n).total * (fp32 ? 4 : 8); }
+int selinv_smem_bytes(int n, bool fp32) { return selinv_layout(n).total * (fp32 ? 4 : 8); }
+int whiten_smem_bytes(int n, int m) { return whiten_layout(n, m).total * 8; }
+
+int max_n_for(const ks_ctx* ctx) {
+    const bool fp32 = ctx->precision == KS_FP32_REFINE;
+    int best = 0;
+    for (int n = 1; n <= KS_NMAX_API; ++n) {
+        if (3 * n + 2 > 256) break;
+        if (tile_smem_bytes(n, fp32) > ctx->smem_optin) break;
+        if (selinv_smem_bytes(n, fp32) > ctx->smem_optin) break;
+        if (whiten_smem_bytes(n, 0) > ctx->smem_optin) break;
+        best = n;
+    }
+    return best;
+}
+
+int max_m_for(const ks_ctx* ctx, int n) {
+    int best = -1;
+    for (int m = 0; m <= KS_NMAX_API; ++m) {
+        if (n + m > 256) break;
+        if (whiten_smem_bytes(n, m) > ctx->smem_optin) break;
+        best = m;
+    }
+    return best;
+}
+
+// Reads the device error words and resets them; returns the most severe code.
+ks_status collect_status(ks_ctx* ctx, int64_t* info) {
+    KS_CUDA(ctx, cudaMemcpyAsync(ctx->h_bad, ctx->d_bad, sizeof(unsigned long long) * ST_NCODES,
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+    KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    KS_CUDA(ctx, cudaMemsetAsync(ctx->d_bad, 0xFF, sizeof(unsigned long long) * ST_NCODES, ctx->stream));
+    static const int order[] = {ST_NOT_SPD, ST_SINGULAR, ST_TIMEOUT, ST_ARG};
+    for (int code : order) {
+        if (ctx->h_bad[code] != ~0ULL) {
+            if (info) *info = (int64_t)ctx->h_bad[code];
+            const char* what = code == ST_NOT_SPD ? "a covariance matrix is not SPD at step"
+                               : code == ST_SINGULAR ? "singular diagonal block of R at state"
+                               : code == ST_TIMEOUT ? "device wait timed out at"
+                                                    : "bad argument detected on device at";
+            return fail(ctx, (ks_status)code, "%s %lld", what, (long long)ctx->h_bad[code]);
+        }
+    }
+    if (info) *info = -1;
+    return KS_OK;
+}
+
+cudaEvent_t get_event(ks_ctx* ctx) {
+    if (!ctx->spare.empty()) {
+        cudaEvent_t e = ctx->spare.back();
+        ctx->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets the launches of one phase: counts them and, with profiling on, records a pair of
+// events on the ctx's stream around them.
+struct Phase {
+    ks_ctx* ctx;
+    int phase;
+    uint64_t l0;
+    cudaEvent_t a = nullptr;
+    Phase(ks_ctx* c, int ph) : ctx(c), phase(ph), l0(t_launches) {
+        if (ctx->profile) {
+            a = get_event(ctx);
+            cudaEventRecord(a, ctx->stream);
+        }
+    }
+    ~Phase() {
+        const uint64_t nl = t_launches - l0;
+        ctx->prof.launches += nl;
+        ctx->prof.phase_launches[phase] += nl;
+        if (ctx->profile && a) {
+            cudaEvent_t b = get_event(ctx);
+            cudaEventRecord(b, ctx->stream);
+            ctx->pending.push_back({phase, a, b});
+        }
+    }
+};
+
+void drain_profile(ks_ctx* ctx) {
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) ctx->prof.phase_ms[p.phase] += ms;
+        cudaGetLastError();
+        ctx->spare.push_back(p.a);
+        ctx->spare.push_back(p.b);
+    }
+    ctx->pending.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+void ks_default_options(ks_options* opt) {
+    if (!opt) return;
+    opt->device = 0;
+    opt->precision = KS_FP64;
+    opt->stream = nullptr;
+    opt->mem_budget = 0;
+    opt->sync = 1;
+    opt->profile = 0;
+}
+
+ks_status ks_create(ks_ctx** out, const ks_options* opt) {
+    if (!out) return KS_ERR_ARG;
+    *out = nullptr;
+    ks_options o;
+    ks_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != KS_FP64 && o.precision != KS_FP32_REFINE) return KS_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || o.device < 0 || o.device >= ndev) {
+        cudaGetLastError();
+        return KS_ERR_CUDA;
+    }
+    ks_ctx* ctx = new ks_ctx();
+    ctx->device = o.device;
+    ctx->precision = o.precision;
+    ctx->budget = o.mem_budget;
+    ctx->sync = o.sync;
+    ctx->profile = o.profile;
+    if (cudaSetDevice(o.device) != cudaSuccess) { delete ctx; return KS_ERR_CUDA; }
+    if (o.stream) {
+        ctx->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return KS_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, o.device);
+    if (cudaMalloc(&ctx->d_bad, sizeof(unsigned long long) * ST_NCODES) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_bad, sizeof(unsigned long long) * ST_NCODES) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_scalar, sizeof(double)) != cudaSuccess) {
+        ks_destroy(ctx);
+        return KS_ERR_OOM;
+    }
+    cudaMemsetAsync(ctx->d_bad, 0xFF, sizeof(unsigned long long) * ST_NCODES, ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        ks_destroy(ctx);
+        return KS_ERR_CUDA;
+    }
+    *out = ctx;
+    return KS_OK;
+}
+
+int ks_max_n(const ks_ctx* ctx) { return ctx ? max_n_for(ctx) : 0; }
+
+int ks_max_m(const ks_ctx* ctx, int n) { return ctx ? max_m_for(ctx, n) : -1; }
+
+const char* ks_last_error(const ks_ctx* ctx) { return ctx ? ctx->err.c_str() : "null ctx"; }
+
+ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const double* F,
+                    const double* H, const double* c, const double* K, const double* G,
+                    const double* o, const double* C, double* u_out, ks_handle* keep,
+                    int64_t* info) {
+    if (!ctx) return KS_ERR_ARG;
+    if (info) *info = -1;
+    ks_fac* reuse = nullptr;
+    if (keep) {
+        if (*keep && ctx->facs.count(*keep)) reuse = *keep;
+        *keep = nullptr;
+    }
+    ctx->err.clear();
+    if (k < 1) return fail(ctx, KS_ERR_ARG, "k must be >= 1 (got %lld)", (long long)k);
+    const int maxn = max_n_for(ctx);
+    if (n < 1 || n > maxn) return fail(ctx, KS_ERR_ARG, "n = %d outside [1, %d]", n, maxn);
+    if (!m || !u_out) return fail(ctx, KS_ERR_ARG, "m and u_out must not be NULL");
+    if (k > 1 && (!F || !H || !K)) return fail(ctx, KS_ERR_ARG, "F, H and K must not be NULL when k > 1");
+    const bool fp32 = ctx->precision == KS_FP32_REFINE;
+    const int maxm = max_m_for(ctx, n);
+    int mmax = 0;
+    int64_t tot_m = 0, tot_m2 = 0;
+    bool uniform = true;
+    for (int64_t i = 0; i < k; ++i) {
+        const int mi = m[i];
+        if (mi < 0 || mi > maxm) return fail(ctx, KS_ERR_ARG, "m[%lld] = %d outside [0, %d]", (long long)i, mi, maxm);
+        mmax = std::max(mmax, mi);
+        tot_m += mi;
+        tot_m2 += (int64_t)mi * mi;
+        uniform = uniform && (mi == m[0]);
+    }
+    if (tot_m > 0 && (!G || !o || !C)) return fail(ctx, KS_ERR_ARG, "G, o and C must not be NULL when some m_i > 0");
+    KS_CUDA(ctx, cudaSetDevice(ctx->device));
+
+    const size_t T = fp32 ? 4 : 8;
+    const int64_t CS = level_cs(n), RS = rstore_rs(n);
+    const int64_t nn = (int64_t)n * n;
+    const int64_t ke = k > 1 ? k - 1 : 0;
+    struct Src { const double* p; size_t count; bool dev; size_t off; };
+    Src src[7] = {{F, (size_t)(ke * nn), false, 0}, {H, (size_t)(ke * nn), false, 0},
+                  {c, (size_t)(ke * n), false, 0},  {K, (size_t)(ke * nn), false, 0},
+                  {G, (size_t)(tot_m * n), false, 0}, {o, (size_t)tot_m, false, 0},
+                  {C, (size_t)tot_m2, false, 0}};
+    Plan plan;
+    const size_t o_lvlA = plan.take((size_t)k * CS * T);
+    const size_t o_lvlB = plan.take((size_t)(k / 2 + 1) * CS * T);
+    for (auto& s : src) {
+        s.dev = s.p == nullptr || s.count == 0 || is_device_ptr(s.p);
+        if (!s.dev) s.off = plan.take(s.count * sizeof(double));
+    }
+    const bool u_dev = is_device_ptr(u_out);
+    const size_t o_u = u_dev ? 0 : plan.take((size_t)k * n * sizeof(double));
+    size_t o_moff = 0, o_goff = 0, o_coff = 0;
+    if (!uniform) {
+        o_moff = plan.take((size_t)k * sizeof(int32_t));
+        o_goff = plan.take((size_t)(k + 1) * sizeof(int64_t));
+        o_coff = plan.take((size_t)(k + 1) * sizeof(int64_t));
+    }
+    size_t o_R = 0, o_res = 0;
+    if (!keep) {
+        o_R = plan.take((size_t)k * RS * T);
+        o_res = plan.take((size_t)2 * k * sizeof(double));
+    }
+    size_t o_LK = 0, o_LC = 0, o_g = 0, o_q = 0, o_w = 0, o_d = 0;
+    if (fp32) {
+        o_LK = plan.take((size_t)ke * nn * sizeof(double));
+        o_LC = plan.take((size_t)std::max<int64_t>(tot_m2, 1) * sizeof(double));
+        o_g = plan.take((size_t)k * n * sizeof(double));
+        o_q = plan.take((size_t)std::max<int64_t>(ke, 1) * n * sizeof(double));
+        o_w = plan.take((size_t)k * n * sizeof(double));
+        o_d = plan.take((size_t)k * n * sizeof(double));
+    }
+    ks_status rs = reserve(ctx, plan.off);
+    if (rs != KS_OK) return rs;
+    char* ws = (char*)ctx->ws;
+    cudaStream_t st = ctx->stream;
+
+    ks_fac* fac = nullptr;
+    void* R;
+    double* resid;
+    if (keep && reuse && reuse->k == k && reuse->n == n && reuse->precision == ctx->precision) {
+        fac = reuse;
+        R = fac->R;
+        resid = fac->resid;
+    } else if (keep) {
+        fac = new ks_fac();
+        fac->k = k;
+        fac->n = n;
+        fac->precision = ctx->precision;
+        cudaError_t e1 = cudaMalloc(&fac->R, (size_t)k * RS * T);
+        cudaError_t e2 = e1 == cudaSuccess ? cudaMalloc((void**)&fac->resid, (size_t)2 * k * sizeof(double)) : e1;
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            cudaGetLastError();
+            if (fac->R) cudaFree(fac->R);
+            delete fac;
+            return fail(ctx, KS_ERR_OOM, "cannot allocate the retained factor (%zu bytes)", (size_t)k * RS * T);
+        }
+        R = fac->R;
+        resid = fac->resid;
+    } else {
+        R = ws + o_R;
+        resid = (double*)(ws + o_res);
+    }
+
+    ctx->prof.calls++;
+    // Stage host inputs.
+    const double* dptr[7];
+    double* u = u_dev ? u_out : (double*)(ws + o_u);
+    std::vector<int64_t> goff, coff;
+    {
+    Phase ph_copy(ctx, KS_PHASE_COPY);
+    for (int i = 0; i < 7; ++i) {
+        if (src[i].dev) {
+            dptr[i] = src[i].p;
+        } else {
+            KS_CUDA(ctx, cudaMemcpyAsync(ws + src[i].off, src[i].p, src[i].count * sizeof(double),
+                                         cudaMemcpyHostToDevice, st));
+            dptr[i] = (const double*)(ws + src[i].off);
+        }
+    }
+    if (!uniform) {
+        goff.resize(k + 1);
+        coff.resize(k + 1);
+        goff[0] = coff[0] = 0;
+        for (int64_t i = 0; i < k; ++i) {
+            goff[i + 1] = goff[i] + m[i];
+            coff[i + 1] = coff[i] + (int64_t)m[i] * m[i];
+        }
+        KS_CUDA(ctx, cudaMemcpyAsync(ws + o_moff, m, (size_t)k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        KS_CUDA(ctx, cudaMemcpyAsync(ws + o_goff, goff.data(), (size_t)(k + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        KS_CUDA(ctx, cudaMemcpyAsync(ws + o_coff, coff.data(), (size_t)(k + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    }
+    }
+
+    WhitenArgs wa;
+    wa.k = k;
+    wa.n = n;
+    wa.mmax = mmax;
+    wa.m_uniform = uniform ? m[0] : -1;
+    wa.m = uniform ? nullptr : (const int32_t*)(ws + o_moff);
+    wa.goff = uniform ? nullptr : (const int64_t*)(ws + o_goff);
+    wa.coff = uniform ? nullptr : (const int64_t*)(ws + o_coff);
+    wa.F = dptr[0]; wa.H = dptr[1]; wa.c = c ? dptr[2] : nullptr; wa.K = dptr[3];
+    wa.G = dptr[4]; wa.o = dptr[5]; wa.C = dptr[6];
+    wa.level0 = ws + o_lvlA;
+    wa.resid = resid + k;
+    wa.LK = fp32 ? (double*)(ws + o_LK) : nullptr;
+    wa.LC = fp32 ? (double*)(ws + o_LC) : nullptr;
+    wa.bad = ctx->d_bad;
+    KS_CUDA(ctx, cudaMemsetAsync(resid, 0, (size_t)k * sizeof(double), st));
+    {
+        Phase ph(ctx, KS_PHASE_WHITEN);
+        KS_CUDA(ctx, launch_whiten(wa, fp32, st));
+    }
+
+    // Odd-even levels.
+    void* bufs[2] = {ws + o_lvlA, ws + o_lvlB};
+    int64_t nc = k;
+    int level = 0, cur = 0;
+    {
+        Phase ph(ctx, KS_PHASE_LEVEL);
+        while (nc > 1) {
+            KS_CUDA(ctx, launch_level(n, nc, level, k, bufs[cur], bufs[cur ^ 1], R, resid, ctx->d_bad, fp32, st));
+            nc /= 2;
+            ++level;
+            cur ^= 1;
+        }
+    }
+    const int L = level;
+    {
+        Phase ph(ctx, KS_PHASE_BACKSUB);
+        KS_CUDA(ctx, launch_base(n, k, L, bufs[cur], R, ctx->d_bad, fp32, st));
+        for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_backsub(n, k, l, R, nullptr, u, fp32, st));
+    }
+
+    if (fp32) {
+        Phase ph(ctx, KS_PHASE_REFINE);
+        RefineArgs ra;
+        ra.k = k;
+        ra.n = n;
+        ra.m_uniform = wa.m_uniform;
+        ra.m = wa.m;
+        ra.goff = wa.goff;
+        ra.coff = wa.coff;
+        ra.F = wa.F; ra.H = wa.H; ra.c = wa.c; ra.G = wa.G; ra.o = wa.o;
+        ra.LK = wa.LK; ra.LC = wa.LC;
+        ra.u = u;
+        ra.g = (double*)(ws + o_g);
+        ra.q = (double*)(ws + o_q);
+        double* w = (double*)(ws + o_w);
+        double* d = (double*)(ws + o_d);
+        KS_CUDA(ctx, launch_refine_gradient(ra, st));
+        for (int l = 0; l <= L; ++l) KS_CUDA(ctx, launch_rt_solve(n, k, l, R, ra.g, w, fp32, st));
+        for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_backsub(n, k, l, R, w, d, fp32, st));
+        KS_CUDA(ctx, launch_axpy(u, d, k * n, st));
+    }
+    if (!u_dev) {
+        Phase ph(ctx, KS_PHASE_COPY);
+        KS_CUDA(ctx, cudaMemcpyAsync(u_out, u, (size_t)k * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+
+    if (fac) {
+        ctx->facs.insert(fac);
+        *keep = fac;
+    }
+    (void)reuse;
+    if (ctx->sync) {
+        ks_status s = collect_status(ctx, info);
+        if (s != KS_OK && fac) {
+            // the handle stays valid (memory owned by ctx) but the factor is unusable
+        }
+        return s;
+    }
+    return KS_OK;
+}
+
+ks_status ks_covariances(ks_ctx* ctx, ks_handle h, double* cov_out, double* cross_out) {
+    if (!ctx) return KS_ERR_ARG;
+    ctx->err.clear();
+    if (!h || !ctx->facs.count(h)) return fail(ctx, KS_ERR_NO_FACTOR, "unknown or released handle");
+    if (!cov_out) return fail(ctx, KS_ERR_ARG, "cov_out must not be NULL");
+    KS_CUDA(ctx, cudaSetDevice(ctx->device));
+    const bool fp32 = h->precision == KS_FP32_REFINE;
+    const int n = h->n;
+    const int64_t k = h->k, nn = (int64_t)n * n;
+    const size_t T = fp32 ? 4 : 8;
+    Plan plan;
+    const size_t o_S = plan.take((size_t)k * 2 * nn * T);
+    const bool cov_dev = is_device_ptr(cov_out);
+    const size_t o_cov = cov_dev ? 0 : plan.take((size_t)k * nn * sizeof(double));
+    const bool cross_dev = cross_out == nullptr || is_device_ptr(cross_out);
+    const size_t o_cross = cross_dev ? 0 : plan.take((size_t)std::max<int64_t>(k - 1, 1) * nn * sizeof(double));
+    ks_status rs = reserve(ctx, plan.off);
+    if (rs != KS_OK) return rs;
+    char* ws = (char*)ctx->ws;
+    cudaStream_t st = ctx->stream;
+    double* Sd = cov_dev ? cov_out : (double*)(ws + o_cov);
+    void* Sx = ws + o_S;
+    int L = 0;
+    while ((k >> (L + 1)) >= 1) ++L;
+    ctx->prof.calls++;
+    double* cr = cross_out ? (cross_dev ? cross_out : (double*)(ws + o_cross)) : nullptr;
+    {
+        Phase ph(ctx, KS_PHASE_SELINV);
+        for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_selinv(n, k, l, h->R, Sx, Sd, ctx->d_bad, fp32, st));
+        if (cr) KS_CUDA(ctx, launch_cross(n, k, Sx, cr, fp32, st));
+    }
+    {
+        Phase ph(ctx, KS_PHASE_COPY);
+        if (cr && !cross_dev && k > 1)
+            KS_CUDA(ctx, cudaMemcpyAsync(cross_out, cr, (size_t)(k - 1) * nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (!cov_dev)
+            KS_CUDA(ctx, cudaMemcpyAsync(cov_out, Sd, (size_t)k * nn * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    if (ctx->sync) return collect_status(ctx, nullptr);
+    return KS_OK;
+}
+
+ks_status ks_residual(ks_ctx* ctx, ks_handle h, double* out) {
+    if (!ctx) return KS_ERR_ARG;
+    if (!h || !ctx->facs.count(h)) return fail(ctx, KS_ERR_NO_FACTOR, "unknown or released handle");
+    if (!out) return fail(ctx, KS_ERR_ARG, "out must not be NULL");
+    KS_CUDA(ctx, cudaSetDevice(ctx->device));
+    Plan plan;
+    const size_t o_s = plan.take(sizeof(double));
+    ks_status rs = reserve(ctx, plan.off);
+    if (rs != KS_OK) return rs;
+    double* d = (double*)((char*)ctx->ws + o_s);
+    KS_CUDA(ctx, launch_sum(h->resid, 2 * h->k, d, ctx->stream));
+    KS_CUDA(ctx, cudaMemcpyAsync(ctx->h_scalar, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *out = *ctx->h_scalar;
+    return KS_OK;
+}
+
+ks_status ks_release(ks_ctx* ctx, ks_handle h) {
+    if (!ctx) return KS_ERR_ARG;
+    if (!h) return KS_OK;
+    if (!ctx->facs.count(h)) return fail(ctx, KS_ERR_NO_FACTOR, "unknown or released handle");
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(h->R);
+    cudaFree(h->resid);
+    ctx->facs.erase(h);
+    delete h;
+    return KS_OK;
+}
+
+ks_status ks_sync(ks_ctx* ctx, int64_t* info) {
+    if (!ctx) return KS_ERR_ARG;
+    KS_CUDA(ctx, cudaSetDevice(ctx->device));
+    return collect_status(ctx, info);
+}
+
+ks_status ks_profile_read(ks_ctx* ctx, ks_profile* out, int reset) {
+    if (!ctx || !out) return KS_ERR_ARG;
+    KS_CUDA(ctx, cudaSetDevice(ctx->device));
+    KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    drain_profile(ctx);
+    *out = ctx->prof;
+    if (reset) ctx->prof = ks_profile{};
+    return KS_OK;
+}
+
+ks_status ks_destroy(ks_ctx* ctx) {
+    if (!ctx) return KS_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drain_profile(ctx);
+    for (cudaEvent_t e : ctx->spare) cudaEventDestroy(e);
+    for (ks_fac* f : ctx->facs) {
+        cudaFree(f->R);
+        cudaFree(f->resid);
+        delete f;
+    }
+    ctx->facs.clear();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_bad) cudaFree(ctx->d_bad);
+    if (ctx->h_bad) cudaFreeHost(ctx->h_bad);
+    if (ctx->h_scalar) cudaFreeHost(ctx->h_scalar);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return KS_OK;
+}
+
+}  // extern "C"

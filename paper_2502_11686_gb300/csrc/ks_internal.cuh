@@ -1,0 +1,165 @@
+// ks_internal.cuh -- layouts, status words and launch wrappers shared by the libks.so sources.
+//
+// Data layout in HBM (all row-major, T = double in KS_FP64 mode, float in KS_FP32_REFINE):
+//
+//  * Level buffer: one record of CS = 3n^2 + 2n elements per alive block column j of the
+//    current level (Section 3: every alive column carries one "C" block and one coupling row to
+//    its left neighbour, so the level problem has the structure of the original one):
+//        [ Chat_j (n x n, upper triangular) | rC_j (n) | E_j (n x 2n) | rE_j (n) ]
+//    E_j = [ left | right ] is the whitened coupling block row between columns j-1 and j with
+//    the coefficients of u_{j-1} (the paper's -B_j) and of u_j (the paper's D_j); E_0 is unused.
+//  * R store: one record of RS = 3n^2 + n elements per ORIGINAL state index c (each block column
+//    is eliminated exactly once, at level l(c) = ctz(c+1)):
+//        [ Rd_c (n x n upper) | Rl_c (n x n, at column c - 2^l) | Rr_c (n x n, at c + 2^l) | y_c (n) ]
+//    Rl exists iff c >= 2^l, Rr iff c + 2^l < k; absent blocks are stored as zeros.
+//  * SelInv store: Sl_c, Sr_c (n x n each, record 2n^2) = S_{c, c-2^l}, S_{c, c+2^l}; the
+//    diagonal blocks S_cc go straight to the covariance output [k][n][n].
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ks {
+
+enum { ST_ARG = 1, ST_NOT_SPD = 2, ST_SINGULAR = 3, ST_TIMEOUT = 6, ST_NCODES = 8 };
+
+// Device error words: bad[code] = smallest failing index seen (ULLONG_MAX = none).
+__device__ __forceinline__ void flag_error(unsigned long long* bad, int code, long long idx) {
+    atomicMin(bad + code, (unsigned long long)idx);
+}
+
+__host__ __device__ __forceinline__ int odd_ld(int x) { return x | 1; }
+__host__ __device__ __forceinline__ int64_t level_cs(int n) { return 3LL * n * n + 2LL * n; }
+__host__ __device__ __forceinline__ int64_t rstore_rs(int n) { return 3LL * n * n + n; }
+
+// Shared-memory layout of one level tile (elements of T).  Leading dimensions are odd so that
+// a warp reading a column (stride ld) hits distinct banks.
+struct TileLayout {
+    int n, ld2, ldf, ld3;
+    int top2, bot2, bf, top3, bot3, scal, total;
+};
+
+__host__ __device__ inline TileLayout tile_layout(int n) {
+    TileLayout L;
+    L.n = n;
+    L.ld2 = odd_ld(3 * n + 1);
+    L.ldf = odd_ld(n);
+    L.ld3 = odd_ld(n + 1);
+    L.top2 = 0;
+    L.bot2 = L.top2 + n * L.ld2;
+    L.bf = L.bot2 + n * L.ld2;
+    L.top3 = L.bf + n * L.ldf;
+    L.bot3 = L.top3 + n * L.ld3;
+    L.scal = L.bot3 + 2 * n * L.ld3;
+    L.total = L.scal + 2 * n;
+    return L;
+}
+
+// Shared-memory layout of the whitening of one step (elements of double).
+struct WhitenLayout {
+    int n, m, ldk, ldw, ldo, ldg, ldt;
+    int kc, w, oc, g, t, top, scal, total;
+};
+
+__host__ __device__ inline WhitenLayout whiten_layout(int n, int m) {
+    WhitenLayout L;
+    L.n = n;
+    L.m = m;
+    L.ldk = odd_ld(n);          // K_i, then its Cholesky factor
+    L.ldw = odd_ld(2 * n + 1);  // [F_i | H_i | c_i], then L_K^{-1} of it
+    L.ldo = odd_ld(m > 0 ? m : 1);
+    L.ldg = odd_ld(n + 1);      // [G_i | o_i], then L_C^{-1} of it
+    L.ldt = odd_ld(n + 1);      // [Chat_i | rC_i] (n rows)
+    L.kc = 0;
+    L.w = L.kc + n * L.ldk;
+    L.oc = L.w + n * L.ldw;
+    L.g = L.oc + m * L.ldo;
+    L.t = L.g + m * L.ldg;
+    L.top = L.t;  // alias: the rhs column of the top block is column n of t
+    L.scal = L.t + n * L.ldt;
+    L.total = L.scal + 2 * n;
+    return L;
+}
+
+// Shared-memory layout of one SelInv column (elements of T).
+struct SelinvLayout {
+    int n, ldr, ldt, lds;
+    int rd, tt, ri, sii, sl, total;
+};
+
+__host__ __device__ inline SelinvLayout selinv_layout(int n) {
+    SelinvLayout L;
+    L.n = n;
+    L.ldr = odd_ld(n);
+    L.ldt = odd_ld(2 * n);
+    L.lds = odd_ld(2 * n);
+    L.rd = 0;
+    L.tt = L.rd + n * L.ldr;     // [Ta | Tb] = Rd^{-1} [Rl | Rr]
+    L.ri = L.tt + n * L.ldt;     // Rd^{-1}
+    L.sii = L.ri + n * L.ldr;    // S_II (2n x 2n)
+    L.sl = L.sii + 2 * n * L.lds;  // [Sl | Sr]
+    L.total = L.sl + n * L.ldt;
+    return L;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Launch wrappers (defined in the .cu files).  All return cudaGetLastError() of the launch and
+// add the number of kernels they launched to t_launches (the calling thread's counter).
+extern thread_local uint64_t t_launches;
+
+struct WhitenArgs {
+    int64_t k;
+    int n, mmax, m_uniform;       // m_uniform >= 0: every m_i equals it; -1: use goff/coff
+    const int32_t* m;             // device [k] (m_uniform < 0)
+    const int64_t* goff;          // device [k+1] row offsets into G/o (m_uniform < 0)
+    const int64_t* coff;          // device [k+1] value offsets into C (m_uniform < 0)
+    const double *F, *H, *c, *K, *G, *o, *C;
+    void* level0;                 // out: level buffer (T), k records
+    double* resid;                // out: [k] rows discarded by the observation pre-reduction
+    double* LK;                   // out (refine mode): [k-1][n][n] Cholesky factors of K_i
+    double* LC;                   // out (refine mode): packed Cholesky factors of C_i
+    unsigned long long* bad;
+};
+
+cudaError_t launch_whiten(const WhitenArgs& a, bool fp32, cudaStream_t st);
+
+cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
+                         void* R, double* resid, unsigned long long* bad, bool fp32,
+                         cudaStream_t st);
+
+cudaError_t launch_base(int n, int64_t k, int L, const void* in, void* R,
+                        unsigned long long* bad, bool fp32, cudaStream_t st);
+
+// Back substitution at one level: u_c = Rd_c^{-1}(rhs_c - Rl_c u_{c-2^l} - Rr_c u_{c+2^l}).
+// rhs = y from the R store when w == nullptr, else w ([k][n] FP64).
+cudaError_t launch_backsub(int n, int64_t k, int level, const void* R, const double* w,
+                           double* u, bool fp32, cudaStream_t st);
+
+// Odd-even SelInv at one level (Algorithm 2 body for every column eliminated at `level`).
+cudaError_t launch_selinv(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
+                          unsigned long long* bad, bool fp32, cudaStream_t st);
+
+// Lag-one blocks cov(u_i, u_{i+1}) gathered from the SelInv store.
+cudaError_t launch_cross(int n, int64_t k, const void* Sx, double* cross, bool fp32,
+                         cudaStream_t st);
+
+// Sum of a [count] FP64 array into *out (single block, deterministic order).
+cudaError_t launch_sum(const double* x, int64_t count, double* out, cudaStream_t st);
+
+// Refinement (KS_FP32_REFINE).  g = (UA)^T U (b - A u) in FP64 (Section 2's normal equations
+// of the whitened system), then R^T w = g level by level, then R d = w, u += d.
+struct RefineArgs {
+    int64_t k;
+    int n, m_uniform;
+    const int32_t* m;
+    const int64_t *goff, *coff;
+    const double *F, *H, *c, *G, *o, *LK, *LC;
+    const double* u;
+    double* g;     // out [k][n]
+    double* q;     // scratch [k-1][n]: K_i^{-1} (F_i u_i + c_i - H_i u_{i+1})
+};
+cudaError_t launch_refine_gradient(const RefineArgs& a, cudaStream_t st);
+cudaError_t launch_rt_solve(int n, int64_t k, int level, const void* R, double* g, double* w,
+                            bool fp32, cudaStream_t st);
+cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t st);
+
+}  // namespace ks

@@ -1,0 +1,396 @@
+// ks_solve.cu -- everything that runs on the finished R factor.
+//
+//  * back substitution through the recursion (Section 3.1): levels from the top down; at level l
+//    every column c with ctz(c+1) = l solves Rd_c u_c = y_c - Rl_c u_{c-2^l} - Rr_c u_{c+2^l};
+//  * odd-even block SelInv (Section 4, Algorithm 2), levels from the top down: with
+//    T = Rd_c^{-1} [Rl_c | Rr_c] and I = {c-2^l, c+2^l},
+//        S_{c,I} = -T S_{I,I},   S_cc = Rd_c^{-1} Rd_c^{-T} - S_{c,I} T^T.
+//    S_{I,I} needs the cross block of the two neighbours a < b; they are adjacent at level l+1,
+//    so the one of them eliminated there holds it (S_ab = Sr_a if ctz(a+1) = l+1, else Sl_b^T);
+//  * the refinement of KS_FP32_REFINE (not in the paper): g = (UA)^T U (b - A u) in FP64, then
+//    the corrected semi-normal equations R^T R d = g with the FP32 R: R^T w = g level by level
+//    from the bottom (column c pulls the blocks of the rows eliminated below it that touch it),
+//    then R d = w by back substitution, u += d.
+#include "ks_internal.cuh"
+
+namespace ks {
+
+constexpr int KS_NMAX = 64;
+
+__device__ __forceinline__ int ctz64(int64_t x) { return __ffsll((long long)x) - 1; }
+
+template <typename TR>
+__global__ void backsub_kernel(int n, int64_t k, int level, const TR* __restrict__ R,
+                               const double* __restrict__ w, double* __restrict__ u) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t c = ((2 * q + 1) << level) - 1;
+    if (c >= k) return;
+    const int nn = n * n;
+    const TR* Rc = R + c * rstore_rs(n);
+    const int64_t a = c - (1LL << level), b = c + (1LL << level);
+    double r[KS_NMAX];
+    for (int i = 0; i < n; ++i) r[i] = w ? w[c * n + i] : (double)Rc[3 * nn + i];
+    if (a >= 0) {
+        const double* ua = u + a * n;
+        for (int i = 0; i < n; ++i) {
+            double s = r[i];
+            for (int p = 0; p < n; ++p) s = fma(-(double)Rc[nn + i * n + p], ua[p], s);
+            r[i] = s;
+        }
+    }
+    if (b < k) {
+        const double* ub = u + b * n;
+        for (int i = 0; i < n; ++i) {
+            double s = r[i];
+            for (int p = 0; p < n; ++p) s = fma(-(double)Rc[2 * nn + i * n + p], ub[p], s);
+            r[i] = s;
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = r[i];
+        for (int p = i + 1; p < n; ++p) s = fma(-(double)Rc[i * n + p], r[p], s);
+        r[i] = s / (double)Rc[i * n + i];
+    }
+    for (int i = 0; i < n; ++i) u[c * n + i] = r[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) selinv_kernel(int n, int64_t k, int level,
+                                                     const T* __restrict__ R, T* __restrict__ Sx,
+                                                     double* __restrict__ Sd,
+                                                     unsigned long long* bad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    const SelinvLayout L = selinv_layout(n);
+    T* RD = sm + L.rd;
+    T* TT = sm + L.tt;
+    T* RI = sm + L.ri;
+    T* SII = sm + L.sii;
+    T* SL = sm + L.sl;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int nn = n * n;
+    const int64_t q = blockIdx.x;
+    const int64_t c = ((2 * q + 1) << level) - 1;
+    if (c >= k) return;
+    const int64_t a = c - (1LL << level), b = c + (1LL << level);
+    const bool ha = a >= 0, hb = b < k;
+    const T* Rc = R + c * rstore_rs(n);
+    const T* Sab = nullptr;
+    bool sab_t = false;
+    if (ha && hb) {
+        if (ctz64(a + 1) == level + 1) {
+            Sab = Sx + a * 2 * nn + nn;  // Sr_a = S_{a,b}
+        } else {
+            Sab = Sx + b * 2 * nn;       // Sl_b = S_{b,a}
+            sab_t = true;
+        }
+    }
+    for (int e = tid; e < nn; e += nth) {
+        const int r = e / n, cc = e - r * n;
+        RD[r * L.ldr + cc] = Rc[e];
+        TT[r * L.ldt + cc] = ha ? Rc[nn + e] : T(0);
+        TT[r * L.ldt + n + cc] = hb ? Rc[2 * nn + e] : T(0);
+        RI[r * L.ldr + cc] = (r == cc) ? T(1) : T(0);
+        SII[r * L.lds + cc] = ha ? (T)Sd[a * nn + e] : T(0);
+        SII[(n + r) * L.lds + n + cc] = hb ? (T)Sd[b * nn + e] : T(0);
+        T x = T(0);
+        if (Sab != nullptr) x = sab_t ? Sab[cc * n + r] : Sab[e];
+        SII[r * L.lds + n + cc] = x;          // S_ab
+        SII[(n + cc) * L.lds + r] = x;        // S_ba = S_ab^T
+    }
+    __syncthreads();
+    // X <- Rd^{-1} X for the 3n columns of [TT | RI] (one thread per column).
+    for (int col = tid; col < 3 * n; col += nth) {
+        T* X = col < 2 * n ? TT + col : RI + (col - 2 * n);
+        const int ldx = col < 2 * n ? L.ldt : L.ldr;
+        for (int i = n - 1; i >= 0; --i) {
+            T s = X[i * ldx];
+            for (int p = i + 1; p < n; ++p) s = fma(-RD[i * L.ldr + p], X[p * ldx], s);
+            X[i * ldx] = s / RD[i * L.ldr + i];
+        }
+    }
+    __syncthreads();
+    // [Sl | Sr] = -T S_II
+    for (int e = tid; e < 2 * nn; e += nth) {
+        const int r = e / (2 * n), cc = e - r * 2 * n;
+        T s = T(0);
+        for (int p = 0; p < 2 * n; ++p) s = fma(TT[r * L.ldt + p], SII[p * L.lds + cc], s);
+        SL[r * L.ldt + cc] = -s;
+    }
+    __syncthreads();
+    // S_cc = Rd^{-1} Rd^{-T} - [Sl | Sr] T^T   (into RD, no longer needed)
+    for (int e = tid; e < nn; e += nth) {
+        const int r = e / n, cc = e - r * n;
+        T s = T(0);
+        for (int p = 0; p < n; ++p) s = fma(RI[r * L.ldr + p], RI[cc * L.ldr + p], s);
+        for (int p = 0; p < 2 * n; ++p) s = fma(-SL[r * L.ldt + p], TT[cc * L.ldt + p], s);
+        RD[r * L.ldr + cc] = s;
+    }
+    __syncthreads();
+    T* Sxc = Sx + c * 2 * nn;
+    for (int e = tid; e < nn; e += nth) {
+        const int r = e / n, cc = e - r * n;
+        const T v = T(0.5) * (RD[r * L.ldr + cc] + RD[cc * L.ldr + r]);
+        Sd[c * nn + e] = (double)v;
+        Sxc[e] = SL[r * L.ldt + cc];
+        Sxc[nn + e] = SL[r * L.ldt + n + cc];
+        if (r == cc && !(v > T(0))) flag_error(bad, ST_SINGULAR, c);
+    }
+}
+
+template <typename T>
+__global__ void cross_kernel(int n, int64_t k, const T* __restrict__ Sx, double* __restrict__ cross) {
+    const int nn = n * n;
+    const int64_t total = (k - 1) * nn;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / nn;
+        const int rc = (int)(e - i * nn), r = rc / n, cc = rc - r * n;
+        double v;
+        if ((i & 1) == 0)
+            v = (double)Sx[i * 2 * nn + nn + rc];              // Sr_i = S_{i,i+1}
+        else
+            v = (double)Sx[(i + 1) * 2 * nn + cc * n + r];     // Sl_{i+1}^T
+        cross[e] = v;
+    }
+}
+
+__global__ void sum_kernel(const double* __restrict__ x, int64_t count, double* out) {
+    __shared__ double part[1024];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) s += x[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
+}
+
+// q_i = K_i^{-1} (F_i u_i + c_i - H_i u_{i+1}) with K_i = L_K L_K^T (one thread per step).
+__global__ void refine_q_kernel(RefineArgs a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i + 1 >= a.k) return;
+    const int n = a.n, nn = n * n;
+    const double* F = a.F + i * nn;
+    const double* H = a.H + i * nn;
+    const double* Lk = a.LK + i * nn;
+    const double* u0 = a.u + i * n;
+    const double* u1 = a.u + (i + 1) * n;
+    double e[KS_NMAX];
+    for (int r = 0; r < n; ++r) {
+        double s = a.c ? a.c[i * n + r] : 0.0;
+        for (int p = 0; p < n; ++p) s = fma(F[r * n + p], u0[p], s);
+        for (int p = 0; p < n; ++p) s = fma(-H[r * n + p], u1[p], s);
+        e[r] = s;
+    }
+    for (int r = 0; r < n; ++r) {  // L y = e
+        double s = e[r];
+        for (int p = 0; p < r; ++p) s = fma(-Lk[r * n + p], e[p], s);
+        e[r] = s / Lk[r * n + r];
+    }
+    for (int r = n - 1; r >= 0; --r) {  // L^T q = y
+        double s = e[r];
+        for (int p = r + 1; p < n; ++p) s = fma(-Lk[p * n + r], e[p], s);
+        e[r] = s / Lk[r * n + r];
+    }
+    for (int r = 0; r < n; ++r) a.q[i * n + r] = e[r];
+}
+
+// g_c = H_{c-1}^T q_{c-1} - F_c^T q_c + G_c^T C_c^{-1} (o_c - G_c u_c).
+__global__ void refine_g_kernel(RefineArgs a) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= a.k) return;
+    const int n = a.n, nn = n * n;
+    double g[KS_NMAX];
+    for (int r = 0; r < n; ++r) g[r] = 0.0;
+    if (c >= 1) {
+        const double* H = a.H + (c - 1) * nn;
+        const double* qv = a.q + (c - 1) * n;
+        for (int r = 0; r < n; ++r)
+            for (int p = 0; p < n; ++p) g[r] = fma(H[p * n + r], qv[p], g[r]);
+    }
+    if (c + 1 < a.k) {
+        const double* F = a.F + c * nn;
+        const double* qv = a.q + c * n;
+        for (int r = 0; r < n; ++r)
+            for (int p = 0; p < n; ++p) g[r] = fma(-F[p * n + r], qv[p], g[r]);
+    }
+    int mi;
+    int64_t go, co;
+    if (a.m_uniform >= 0) {
+        mi = a.m_uniform;
+        go = c * mi;
+        co = c * (int64_t)mi * mi;
+    } else {
+        mi = a.m[c];
+        go = a.goff[c];
+        co = a.coff[c];
+    }
+    if (mi > 0) {
+        const double* G = a.G + go * n;
+        const double* Lc = a.LC + co;
+        const double* uc = a.u + c * n;
+        double v[KS_NMAX];
+        for (int r = 0; r < mi; ++r) {
+            double s = a.o[go + r];
+            for (int p = 0; p < n; ++p) s = fma(-G[r * n + p], uc[p], s);
+            v[r] = s;
+        }
+        for (int r = 0; r < mi; ++r) {
+            double s = v[r];
+            for (int p = 0; p < r; ++p) s = fma(-Lc[r * mi + p], v[p], s);
+            v[r] = s / Lc[r * mi + r];
+        }
+        for (int r = mi - 1; r >= 0; --r) {
+            double s = v[r];
+            for (int p = r + 1; p < mi; ++p) s = fma(-Lc[p * mi + r], v[p], s);
+            v[r] = s / Lc[r * mi + r];
+        }
+        for (int r = 0; r < n; ++r)
+            for (int p = 0; p < mi; ++p) g[r] = fma(G[p * n + r], v[p], g[r]);
+    }
+    for (int r = 0; r < n; ++r) a.g[c * n + r] = g[r];
+}
+
+// R^T w = g at one level: every column alive at `level` first pulls the blocks of the rows
+// eliminated at level-1 that touch it (rows c -+ 2^{level-1}), then, if it is eliminated at
+// `level`, solves Rd_c^T w_c = g_c.
+template <typename TR>
+__global__ void rt_solve_kernel(int n, int64_t k, int level, const TR* __restrict__ R,
+                                double* __restrict__ g, double* __restrict__ w) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= (k >> level)) return;
+    const int64_t c = ((j + 1) << level) - 1;
+    const int nn = n * n;
+    const int64_t RS = rstore_rs(n);
+    double r[KS_NMAX];
+    for (int i = 0; i < n; ++i) r[i] = g[c * n + i];
+    if (level >= 1) {
+        const int64_t h = 1LL << (level - 1);
+        if (c - h >= 0) {  // row c-h has its right block Rr at column c
+            const TR* Rr = R + (c - h) * RS + 2 * nn;
+            const double* wr = w + (c - h) * n;
+            for (int i = 0; i < n; ++i) {
+                double s = r[i];
+                for (int p = 0; p < n; ++p) s = fma(-(double)Rr[p * n + i], wr[p], s);
+                r[i] = s;
+            }
+        }
+        if (c + h < k) {  // row c+h has its left block Rl at column c
+            const TR* Rl = R + (c + h) * RS + nn;
+            const double* wr = w + (c + h) * n;
+            for (int i = 0; i < n; ++i) {
+                double s = r[i];
+                for (int p = 0; p < n; ++p) s = fma(-(double)Rl[p * n + i], wr[p], s);
+                r[i] = s;
+            }
+        }
+    }
+    if (ctz64(c + 1) == level) {
+        const TR* Rd = R + c * RS;
+        for (int i = 0; i < n; ++i) {
+            double s = r[i];
+            for (int p = 0; p < i; ++p) s = fma(-(double)Rd[p * n + i], r[p], s);
+            r[i] = s / (double)Rd[i * n + i];
+        }
+        for (int i = 0; i < n; ++i) w[c * n + i] = r[i];
+    } else {
+        for (int i = 0; i < n; ++i) g[c * n + i] = r[i];
+    }
+}
+
+__global__ void axpy_kernel(double* __restrict__ u, const double* __restrict__ d, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        u[i] += d[i];
+}
+
+static unsigned grid_for(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (1LL << 30)) b = 1LL << 30;
+    return (unsigned)b;
+}
+
+cudaError_t launch_backsub(int n, int64_t k, int level, const void* R, const double* w,
+                           double* u, bool fp32, cudaStream_t st) {
+    const int64_t cols = ((k >> level) + 1) / 2;
+    const int threads = 128;
+    if (fp32)
+        backsub_kernel<float><<<grid_for(cols, threads), threads, 0, st>>>(n, k, level, (const float*)R, w, u);
+    else
+        backsub_kernel<double><<<grid_for(cols, threads), threads, 0, st>>>(n, k, level, (const double*)R, w, u);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_selinv(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
+                          unsigned long long* bad, bool fp32, cudaStream_t st) {
+    const int64_t cols = ((k >> level) + 1) / 2;
+    const SelinvLayout L = selinv_layout(n);
+    const int threads = 128;
+    const unsigned blocks = (unsigned)cols;
+    if (fp32) {
+        const size_t smem = sizeof(float) * (size_t)L.total;
+        cudaFuncSetAttribute(selinv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        selinv_kernel<float><<<blocks, threads, smem, st>>>(n, k, level, (const float*)R, (float*)Sx, Sd, bad);
+        ++t_launches;
+    } else {
+        const size_t smem = sizeof(double) * (size_t)L.total;
+        cudaFuncSetAttribute(selinv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        selinv_kernel<double><<<blocks, threads, smem, st>>>(n, k, level, (const double*)R, (double*)Sx, Sd, bad);
+        ++t_launches;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cross(int n, int64_t k, const void* Sx, double* cross, bool fp32,
+                         cudaStream_t st) {
+    if (k < 2) return cudaSuccess;
+    const int64_t total = (k - 1) * (int64_t)n * n;
+    if (fp32)
+        cross_kernel<float><<<grid_for(total, 256), 256, 0, st>>>(n, k, (const float*)Sx, cross);
+    else
+        cross_kernel<double><<<grid_for(total, 256), 256, 0, st>>>(n, k, (const double*)Sx, cross);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+thread_local uint64_t t_launches = 0;
+
+cudaError_t launch_sum(const double* x, int64_t count, double* out, cudaStream_t st) {
+    sum_kernel<<<1, 1024, 0, st>>>(x, count, out);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_gradient(const RefineArgs& a, cudaStream_t st) {
+    if (a.k > 1) {
+        refine_q_kernel<<<grid_for(a.k - 1, 128), 128, 0, st>>>(a);
+        ++t_launches;
+    }
+    refine_g_kernel<<<grid_for(a.k, 128), 128, 0, st>>>(a);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rt_solve(int n, int64_t k, int level, const void* R, double* g, double* w,
+                            bool fp32, cudaStream_t st) {
+    const int64_t cols = k >> level;
+    if (fp32)
+        rt_solve_kernel<float><<<grid_for(cols, 128), 128, 0, st>>>(n, k, level, (const float*)R, g, w);
+    else
+        rt_solve_kernel<double><<<grid_for(cols, 128), 128, 0, st>>>(n, k, level, (const double*)R, g, w);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t st) {
+    axpy_kernel<<<grid_for(count, 256) > 4096 ? 4096 : grid_for(count, 256), 256, 0, st>>>(u, d, count);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace ks

@@ -1,0 +1,184 @@
+"""ctypes binding of libks.so with the C ABI's own names (argument marshalling only).
+
+Every step of the smoother runs in the library's CUDA kernels; nothing here computes.  Arrays
+may be torch tensors (device or host) or numpy arrays (host); they are passed as raw pointers.
+If libks.so has not been built, the first call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libks.so")
+
+KS_OK, KS_ERR_ARG, KS_ERR_NOT_SPD, KS_ERR_SINGULAR, KS_ERR_OOM, KS_ERR_CUDA, KS_ERR_TIMEOUT, \
+    KS_ERR_NO_FACTOR = range(8)
+STATUS_NAMES = {0: "KS_OK", 1: "KS_ERR_ARG", 2: "KS_ERR_NOT_SPD", 3: "KS_ERR_SINGULAR",
+                4: "KS_ERR_OOM", 5: "KS_ERR_CUDA", 6: "KS_ERR_TIMEOUT", 7: "KS_ERR_NO_FACTOR"}
+KS_FP64, KS_FP32_REFINE = 0, 1
+
+# Every symbol include/ks.h declares.
+EXPORTS = ("ks_default_options", "ks_create", "ks_smooth", "ks_covariances", "ks_residual",
+           "ks_release", "ks_sync", "ks_destroy", "ks_last_error", "ks_max_n", "ks_max_m",
+           "ks_profile_read")
+PHASES = ("whiten", "level", "backsub", "refine", "selinv", "copy")
+
+
+class ks_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("precision", ctypes.c_int),
+                ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
+                ("sync", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class ks_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("phase_launches", ctypes.c_uint64 * 6),
+                ("phase_ms", ctypes.c_double * 6), ("calls", ctypes.c_uint64)]
+
+
+class KsError(RuntimeError):
+    def __init__(self, status: int, message: str, info: int = -1):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}"
+                         + (f" (info={info})" if info >= 0 else ""))
+        self.status = status
+        self.info = info
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Loads libks.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; "
+                               "g.build()'` first (there is no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.ks_default_options.argtypes = [ctypes.POINTER(ks_options)]
+        lib.ks_default_options.restype = None
+        lib.ks_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(ks_options)]
+        lib.ks_create.restype = I
+        lib.ks_smooth.argtypes = [P, I64, I, P, P, P, P, P, P, P, P, P, ctypes.POINTER(P),
+                                  ctypes.POINTER(I64)]
+        lib.ks_smooth.restype = I
+        lib.ks_covariances.argtypes = [P, P, P, P]
+        lib.ks_covariances.restype = I
+        lib.ks_residual.argtypes = [P, P, ctypes.POINTER(ctypes.c_double)]
+        lib.ks_residual.restype = I
+        lib.ks_release.argtypes = [P, P]
+        lib.ks_release.restype = I
+        lib.ks_sync.argtypes = [P, ctypes.POINTER(I64)]
+        lib.ks_sync.restype = I
+        lib.ks_destroy.argtypes = [P]
+        lib.ks_destroy.restype = I
+        lib.ks_last_error.argtypes = [P]
+        lib.ks_last_error.restype = ctypes.c_char_p
+        lib.ks_max_n.argtypes = [P]
+        lib.ks_max_n.restype = I
+        lib.ks_max_m.argtypes = [P, I]
+        lib.ks_max_m.restype = I
+        lib.ks_profile_read.argtypes = [P, ctypes.POINTER(ks_profile), I]
+        lib.ks_profile_read.restype = I
+        _lib = lib
+        return lib
+
+
+def ptr(a):
+    """Raw address of a torch tensor / numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("arrays must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(ctx, st, info=-1):
+    if st != KS_OK:
+        raise KsError(st, ks_last_error(ctx), info)
+
+
+def ks_default_options() -> ks_options:
+    o = ks_options()
+    load().ks_default_options(ctypes.byref(o))
+    return o
+
+
+def ks_create(opts: ks_options | None = None):
+    ctx = ctypes.c_void_p()
+    st = load().ks_create(ctypes.byref(ctx), ctypes.byref(opts) if opts is not None else None)
+    if st != KS_OK:
+        raise KsError(st, "ks_create failed")
+    return ctx
+
+
+def ks_smooth(ctx, k, n, m, F, H, c, K, G, o, C, u_out, keep=False, check=True, reuse=None):
+    """Returns (status, handle or None, info).  With check=True a failure raises KsError.
+    ``reuse``: a handle from an earlier call whose memory the library may reuse (keep=True)."""
+    h = ctypes.c_void_p(reuse.value if reuse is not None else None)
+    info = ctypes.c_int64(-1)
+    st = load().ks_smooth(ctx, int(k), int(n), ptr(m), ptr(F), ptr(H), ptr(c), ptr(K), ptr(G),
+                          ptr(o), ptr(C), ptr(u_out), ctypes.byref(h) if keep else None,
+                          ctypes.byref(info))
+    if check:
+        _check(ctx, st, info.value)
+    return st, (h if keep and h.value else None), info.value
+
+
+def ks_covariances(ctx, h, cov_out, cross_out=None, check=True):
+    st = load().ks_covariances(ctx, h, ptr(cov_out), ptr(cross_out))
+    if check:
+        _check(ctx, st)
+    return st
+
+
+def ks_residual(ctx, h) -> float:
+    v = ctypes.c_double(0.0)
+    _check(ctx, load().ks_residual(ctx, h, ctypes.byref(v)))
+    return v.value
+
+
+def ks_release(ctx, h):
+    return load().ks_release(ctx, h)
+
+
+def ks_sync(ctx):
+    info = ctypes.c_int64(-1)
+    st = load().ks_sync(ctx, ctypes.byref(info))
+    return st, info.value
+
+
+def ks_destroy(ctx):
+    return load().ks_destroy(ctx)
+
+
+def ks_last_error(ctx) -> str:
+    return load().ks_last_error(ctx).decode()
+
+
+def ks_max_n(ctx) -> int:
+    return load().ks_max_n(ctx)
+
+
+def ks_max_m(ctx, n) -> int:
+    return load().ks_max_m(ctx, int(n))
+
+
+def ks_profile_read(ctx, reset=False) -> dict:
+    """Launch counts and per-phase GPU milliseconds of a ctx (see include/ks.h)."""
+    pr = ks_profile()
+    _check(ctx, load().ks_profile_read(ctx, ctypes.byref(pr), 1 if reset else 0))
+    return {"launches": int(pr.launches), "calls": int(pr.calls),
+            "phase_launches": {PHASES[i]: int(pr.phase_launches[i]) for i in range(6)},
+            "phase_ms": {PHASES[i]: float(pr.phase_ms[i]) for i in range(6)}}

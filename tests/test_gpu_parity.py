@@ -1,0 +1,209 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
+
+Tolerances (FP64 mode): relative error <= 1e-10 for the states (2-norm over the concatenated
+vector) and for every covariance block (Frobenius norm per block, worst block).  FP32 +
+refinement mode: states <= 1e-6; the FP32 covariances carry ~cond * 6e-8 and are bounded
+loosely (the paper fixes no FP32 target).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_11686_gb300 import Smoother, inputs, native, problem_arrays
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def rel_states(u, ref):
+    return float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+
+
+def rel_cov(c, ref):
+    num = np.linalg.norm((c - ref).reshape(len(ref), -1), axis=1)
+    den = np.linalg.norm(ref.reshape(len(ref), -1), axis=1)
+    return float(np.max(num / den))
+
+
+@pytest.fixture(scope="module")
+def sm64():
+    s = Smoother(device=0, precision="fp64")
+    yield s
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def sm32():
+    s = Smoother(device=0, precision="fp32_refine")
+    yield s
+    s.close()
+
+
+def run(sm, p, cov=True, cross=False, host=False):
+    arr = problem_arrays(p, None if host else "cuda")
+    u, h = sm.smooth(p.k, p.n, arr, keep=True)
+    like = arr["F"] if arr["F"] is not None else arr["G"]
+    out = {"u": u if host else u.cpu().numpy()}
+    if cov:
+        res = sm.covariances(h, p.k, p.n, like, cross=cross)
+        if cross:
+            c, x = res
+            out["cross"] = x if host else x.cpu().numpy()
+        else:
+            c = res
+        out["cov"] = c if host else c.cpu().numpy()
+    out["resid2"] = sm.residual(h)
+    sm.release(h)
+    return out
+
+
+GRID_K = [1, 2, 3, 4, 5, 6, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 129]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 8])
+def test_fp64_grid(sm64, n):
+    for k in GRID_K:
+        p = inputs.random_problem(k, n, n, seed=1000 * n + k, with_c=True)
+        ref = oracle.smooth(p, cross=True)
+        got = run(sm64, p, cross=True)
+        assert rel_states(got["u"], ref["u"]) < TOL64, (k, n)
+        assert rel_cov(got["cov"], ref["cov"]) < TOL64, (k, n)
+        if k > 1:
+            assert rel_cov(got["cross"], ref["cross"]) < TOL64, (k, n)
+        assert abs(got["resid2"] - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"]), (k, n)
+
+
+@pytest.mark.parametrize("pattern", ["gaps", "wide", "narrow", "zero_first"])
+@pytest.mark.parametrize("k", [7, 33, 100])
+def test_fp64_ragged_observations(sm64, pattern, k):
+    n = 4
+    rng = np.random.default_rng(k)
+    if pattern == "gaps":
+        m = np.where(rng.uniform(size=k) < 0.4, 0, n).astype(np.int32)
+        m[0] = n
+    elif pattern == "wide":
+        m = rng.integers(n, 2 * n + 3, size=k).astype(np.int32)
+    elif pattern == "narrow":
+        m = rng.integers(1, n + 1, size=k).astype(np.int32)
+        m[0] = n
+    else:
+        m = np.full(k, n, np.int32)
+        m[0] = 0
+    p = inputs.random_problem(k, n, m, seed=k + 3, with_c=True)
+    ref = oracle.smooth(p)
+    got = run(sm64, p)
+    assert rel_states(got["u"], ref["u"]) < TOL64
+    assert rel_cov(got["cov"], ref["cov"]) < TOL64
+
+
+def test_fp64_constant_velocity_workload(sm64):
+    """k = 1000, n = 4, m = 2, the 2-D constant-velocity workload: states and all covariances."""
+    p = inputs.cv_problem(k=1000, seed=0)
+    ref = oracle.smooth(p, cross=True)
+    got = run(sm64, p, cross=True)
+    assert rel_states(got["u"], ref["u"]) < TOL64
+    assert rel_cov(got["cov"], ref["cov"]) < TOL64
+    assert rel_cov(got["cross"], ref["cross"]) < TOL64
+
+
+@pytest.mark.parametrize("m", [48, 24])
+def test_fp64_dense_blocks_n48(sm64, m):
+    p = inputs.random_problem(129, 48, m, seed=m, f_scale=0.995)
+    ref = oracle.smooth(p)
+    got = run(sm64, p)
+    assert rel_states(got["u"], ref["u"]) < TOL64
+    assert rel_cov(got["cov"], ref["cov"]) < TOL64
+
+
+def test_fp64_max_n(sm64):
+    n = sm64.max_n
+    p = inputs.random_problem(11, n, n, seed=5)
+    ref = oracle.smooth(p)
+    got = run(sm64, p)
+    assert rel_states(got["u"], ref["u"]) < TOL64
+    assert rel_cov(got["cov"], ref["cov"]) < TOL64
+
+
+def test_fp64_full_size_long_problem(sm64):
+    """k = 1,000,000, n = m = 6: every state and every covariance block against the oracle."""
+    p = inputs.random_problem(1_000_000, 6, 6, seed=0, f_scale=0.99)
+    ref = oracle.smooth(p)
+    got = run(sm64, p)
+    assert rel_states(got["u"], ref["u"]) < TOL64
+    assert rel_cov(got["cov"], ref["cov"]) < TOL64
+
+
+def test_host_and_device_pointers_agree_bitwise(sm64):
+    p = inputs.random_problem(777, 5, 3, seed=9, with_c=True)
+    a = run(sm64, p, host=True)
+    b = run(sm64, p, host=False)
+    assert np.array_equal(a["u"], b["u"])
+    assert np.array_equal(a["cov"], b["cov"])
+
+
+def test_deterministic(sm64):
+    p = inputs.random_problem(5000, 6, 6, seed=4)
+    a = run(sm64, p)
+    b = run(sm64, p)
+    assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["cov"], b["cov"])
+    assert a["resid2"] == b["resid2"]
+
+
+def test_exact_recovery(sm64):
+    p = inputs.consistent_problem(3001, 4, 4, seed=2)
+    got = run(sm64, p, cov=False)
+    assert rel_states(got["u"], p.truth) < TOL64
+    assert got["resid2"] < 1e-18 * float(np.sum(p.o ** 2))
+
+
+def test_not_spd_reports_step(sm64):
+    p = inputs.random_problem(10, 3, 3, seed=2)
+    p.K = p.K.copy()
+    p.K[4] = -np.eye(3)
+    arr = problem_arrays(p, "cuda")
+    with pytest.raises(native.KsError) as ei:
+        sm64.smooth(p.k, p.n, arr)
+    assert ei.value.status == native.KS_ERR_NOT_SPD and ei.value.info == 4
+
+
+def test_unobservable_is_singular(sm64):
+    p = inputs.random_problem(6, 3, 0, seed=2)
+    arr = problem_arrays(p, "cuda")
+    with pytest.raises(native.KsError) as ei:
+        sm64.smooth(p.k, p.n, arr)
+    assert ei.value.status == native.KS_ERR_SINGULAR
+
+
+def test_bad_arguments(sm64):
+    p = inputs.random_problem(4, 3, 3, seed=2)
+    arr = problem_arrays(p, "cuda")
+    with pytest.raises(native.KsError) as ei:
+        sm64.smooth(p.k, sm64.max_n + 1, arr)
+    assert ei.value.status == native.KS_ERR_ARG
+    bad_m = np.full(4, 10_000, np.int32)
+    arr["m"] = bad_m
+    with pytest.raises(native.KsError) as ei:
+        sm64.smooth(p.k, p.n, arr)
+    assert ei.value.status == native.KS_ERR_ARG
+
+
+# ---------------------------------------------------------------- FP32 + FP64 refinement
+
+@pytest.mark.parametrize("n", [1, 2, 4, 6, 8])
+def test_refine_grid(sm32, n):
+    for k in GRID_K:
+        p = inputs.random_problem(k, n, n, seed=77 * n + k, with_c=True)
+        ref = oracle.smooth(p)
+        got = run(sm32, p)
+        assert rel_states(got["u"], ref["u"]) < 1e-6, (k, n)
+        assert rel_cov(got["cov"], ref["cov"]) < 1e-3, (k, n)
+
+
+@pytest.mark.parametrize("n,m,k", [(6, 6, 100_000), (48, 48, 600), (48, 24, 600), (16, 8, 3000)])
+def test_refine_workloads(sm32, n, m, k):
+    p = inputs.random_problem(k, n, m, seed=n + m, f_scale=0.995 if n == 48 else 0.99)
+    ref = oracle.smooth(p)
+    got = run(sm32, p)
+    assert rel_states(got["u"], ref["u"]) < 1e-6
+    assert rel_cov(got["cov"], ref["cov"]) < 1e-3
