@@ -28,8 +28,25 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+SMALL_UNIT = "ks_small_n.cu"   # compiled once per state dimension N = 1..SMALL_NMAX
+SMALL_NMAX = 8
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+
+
+def units():
+    """(source, object name, extra flags) of every translation unit."""
+    out = []
+    for src in sources():
+        base = os.path.basename(src)[:-3]
+        if os.path.basename(src) == SMALL_UNIT:
+            for n in range(1, SMALL_NMAX + 1):
+                out.append((src, f"{base}{n}.o", [f"-DKS_SMALL_N={n}"]))
+        else:
+            out.append((src, base + ".o", []))
+    return out
 
 
 def _digest() -> str:
@@ -54,9 +71,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     cc = nvcc()
     objs = []
 
-    def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+    def compile_one(unit):
+        src, oname, defs = unit
+        obj = os.path.join(BUILD_DIR, oname)
+        cmd = [cc, *NVCC_FLAGS, *defs, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -64,8 +82,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, sources()))
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, units()))
     tmp = LIB + f".tmp{os.getpid()}"
     r = subprocess.run([cc, "-shared", GENCODE, "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:

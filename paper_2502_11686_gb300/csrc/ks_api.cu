@@ -17,10 +17,22 @@
 
 using namespace ks;
 
+namespace ks {
+extern const SmallOps small_ops_1, small_ops_2, small_ops_3, small_ops_4, small_ops_5,
+    small_ops_6, small_ops_7, small_ops_8;
+const SmallOps* small_ops(int n) {
+    static const SmallOps* table[SMALL_NMAX + 1] = {nullptr,      &small_ops_1, &small_ops_2,
+                                                    &small_ops_3, &small_ops_4, &small_ops_5,
+                                                    &small_ops_6, &small_ops_7, &small_ops_8};
+    return (n >= 1 && n <= SMALL_NMAX) ? table[n] : nullptr;
+}
+}  // namespace ks
+
 struct ks_fac {
     int64_t k = 0;
     int n = 0;
     int precision = 0;
+    const SmallOps* small = nullptr;  // small-state path (element-major layouts) or generic
     void* R = nullptr;        // R store, k records of 3n^2+n elements (T)
     double* resid = nullptr;  // [2k]: residual parts of the level tiles and of the whitening
 };
@@ -296,6 +308,8 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     }
     if (tot_m > 0 && (!G || !o || !C)) return fail(ctx, KS_ERR_ARG, "G, o and C must not be NULL when some m_i > 0");
     KS_CUDA(ctx, cudaSetDevice(ctx->device));
+    // Small states with at most n observations per step run one thread per unit of work.
+    const SmallOps* sops = (mmax <= n) ? small_ops(n) : nullptr;
 
     const size_t T = fp32 ? 4 : 8;
     const int64_t CS = level_cs(n), RS = rstore_rs(n);
@@ -326,6 +340,8 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
         o_R = plan.take((size_t)k * RS * T);
         o_res = plan.take((size_t)2 * k * sizeof(double));
     }
+    const size_t o_cn2 = plan.take((size_t)k * n * sizeof(double));
+    const size_t o_cd2 = plan.take((size_t)k * n * sizeof(double));
     size_t o_LK = 0, o_LC = 0, o_g = 0, o_q = 0, o_w = 0, o_d = 0;
     if (fp32) {
         o_LK = plan.take((size_t)ke * nn * sizeof(double));
@@ -343,7 +359,8 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     ks_fac* fac = nullptr;
     void* R;
     double* resid;
-    if (keep && reuse && reuse->k == k && reuse->n == n && reuse->precision == ctx->precision) {
+    if (keep && reuse && reuse->k == k && reuse->n == n && reuse->precision == ctx->precision &&
+        reuse->small == sops) {
         fac = reuse;
         R = fac->R;
         resid = fac->resid;
@@ -352,6 +369,7 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
         fac->k = k;
         fac->n = n;
         fac->precision = ctx->precision;
+        fac->small = sops;
         cudaError_t e1 = cudaMalloc(&fac->R, (size_t)k * RS * T);
         cudaError_t e2 = e1 == cudaSuccess ? cudaMalloc((void**)&fac->resid, (size_t)2 * k * sizeof(double)) : e1;
         if (e1 != cudaSuccess || e2 != cudaSuccess) {
@@ -411,11 +429,13 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     wa.resid = resid + k;
     wa.LK = fp32 ? (double*)(ws + o_LK) : nullptr;
     wa.LC = fp32 ? (double*)(ws + o_LC) : nullptr;
+    wa.cn2 = (double*)(ws + o_cn2);
+    wa.cd2 = (double*)(ws + o_cd2);
     wa.bad = ctx->d_bad;
     KS_CUDA(ctx, cudaMemsetAsync(resid, 0, (size_t)k * sizeof(double), st));
     {
         Phase ph(ctx, KS_PHASE_WHITEN);
-        KS_CUDA(ctx, launch_whiten(wa, fp32, st));
+        KS_CUDA(ctx, sops ? sops->whiten(wa, fp32, st) : launch_whiten(wa, fp32, st));
     }
 
     // Odd-even levels.
@@ -425,7 +445,10 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     {
         Phase ph(ctx, KS_PHASE_LEVEL);
         while (nc > 1) {
-            KS_CUDA(ctx, launch_level(n, nc, level, k, bufs[cur], bufs[cur ^ 1], R, resid, ctx->d_bad, fp32, st));
+            if (sops)
+                KS_CUDA(ctx, sops->level(nc, level, k, bufs[cur], bufs[cur ^ 1], R, resid, wa.cn2, wa.cd2, ctx->d_bad, fp32, st));
+            else
+                KS_CUDA(ctx, launch_level(n, nc, level, k, bufs[cur], bufs[cur ^ 1], R, resid, wa.cn2, wa.cd2, ctx->d_bad, fp32, st));
             nc /= 2;
             ++level;
             cur ^= 1;
@@ -434,8 +457,13 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     const int L = level;
     {
         Phase ph(ctx, KS_PHASE_BACKSUB);
-        KS_CUDA(ctx, launch_base(n, k, L, bufs[cur], R, ctx->d_bad, fp32, st));
-        for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_backsub(n, k, l, R, nullptr, u, fp32, st));
+        if (sops) {
+            KS_CUDA(ctx, sops->base(k, L, bufs[cur], R, wa.cn2, wa.cd2, ctx->d_bad, fp32, st));
+            for (int l = L; l >= 0; --l) KS_CUDA(ctx, sops->backsub(k, l, R, nullptr, u, fp32, st));
+        } else {
+            KS_CUDA(ctx, launch_base(n, k, L, bufs[cur], R, wa.cn2, wa.cd2, ctx->d_bad, fp32, st));
+            for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_backsub(n, k, l, R, nullptr, u, fp32, st));
+        }
     }
 
     if (fp32) {
@@ -455,8 +483,10 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
         double* w = (double*)(ws + o_w);
         double* d = (double*)(ws + o_d);
         KS_CUDA(ctx, launch_refine_gradient(ra, st));
-        for (int l = 0; l <= L; ++l) KS_CUDA(ctx, launch_rt_solve(n, k, l, R, ra.g, w, fp32, st));
-        for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_backsub(n, k, l, R, w, d, fp32, st));
+        for (int l = 0; l <= L; ++l)
+            KS_CUDA(ctx, sops ? sops->rt_solve(k, l, R, ra.g, w, fp32, st) : launch_rt_solve(n, k, l, R, ra.g, w, fp32, st));
+        for (int l = L; l >= 0; --l)
+            KS_CUDA(ctx, sops ? sops->backsub(k, l, R, w, d, fp32, st) : launch_backsub(n, k, l, R, w, d, fp32, st));
         KS_CUDA(ctx, launch_axpy(u, d, k * n, st));
     }
     if (!u_dev) {
@@ -507,8 +537,11 @@ ks_status ks_covariances(ks_ctx* ctx, ks_handle h, double* cov_out, double* cros
     double* cr = cross_out ? (cross_dev ? cross_out : (double*)(ws + o_cross)) : nullptr;
     {
         Phase ph(ctx, KS_PHASE_SELINV);
-        for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_selinv(n, k, l, h->R, Sx, Sd, ctx->d_bad, fp32, st));
-        if (cr) KS_CUDA(ctx, launch_cross(n, k, Sx, cr, fp32, st));
+        const SmallOps* sops = h->small;
+        for (int l = L; l >= 0; --l)
+            KS_CUDA(ctx, sops ? sops->selinv(k, l, h->R, Sx, Sd, ctx->d_bad, fp32, st)
+                              : launch_selinv(n, k, l, h->R, Sx, Sd, ctx->d_bad, fp32, st));
+        if (cr) KS_CUDA(ctx, sops ? sops->cross(k, Sx, cr, fp32, st) : launch_cross(n, k, Sx, cr, fp32, st));
     }
     {
         Phase ph(ctx, KS_PHASE_COPY);

@@ -117,17 +117,37 @@ struct WhitenArgs {
     double* resid;                // out: [k] rows discarded by the observation pre-reduction
     double* LK;                   // out (refine mode): [k-1][n][n] Cholesky factors of K_i
     double* LC;                   // out (refine mode): packed Cholesky factors of C_i
+    double* cn2;                  // out [k][n]: |Chat_i col|^2 + |B_i col|^2 (state i)
+    double* cd2;                  // out [k][n]: |D_{i-1} col|^2 (state i; row 0 = 0)
     unsigned long long* bad;
 };
+
+// Numerical singularity test of a finished diagonal block of R: |R_ii| is compared with the
+// 2-norm of column i of the whitened matrix U A for that state (orthogonal transformations
+// keep column norms, so |R_ii| <= that norm, and a ratio at rounding level means the column is
+// dependent on the columns eliminated before it).
+template <typename T>
+__host__ __device__ __forceinline__ double singular_tol(int n);
+template <>
+__host__ __device__ __forceinline__ double singular_tol<double>(int n) { return 4.0 * n * 2.220446049250313e-16; }
+template <>
+__host__ __device__ __forceinline__ double singular_tol<float>(int n) { return 1.0 * n * 1.1920928955078125e-7; }
+
+template <typename T>
+__device__ __forceinline__ bool diag_is_singular(T d, double colnorm2, int n) {
+    const double dd = (double)d;
+    const double tol = singular_tol<T>(n);
+    return !(dd * dd > tol * tol * colnorm2) || !isfinite(dd);
+}
 
 cudaError_t launch_whiten(const WhitenArgs& a, bool fp32, cudaStream_t st);
 
 cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
-                         void* R, double* resid, unsigned long long* bad, bool fp32,
-                         cudaStream_t st);
+                         void* R, double* resid, const double* cn2, const double* cd2,
+                         unsigned long long* bad, bool fp32, cudaStream_t st);
 
-cudaError_t launch_base(int n, int64_t k, int L, const void* in, void* R,
-                        unsigned long long* bad, bool fp32, cudaStream_t st);
+cudaError_t launch_base(int n, int64_t k, int L, const void* in, void* R, const double* cn2,
+                        const double* cd2, unsigned long long* bad, bool fp32, cudaStream_t st);
 
 // Back substitution at one level: u_c = Rd_c^{-1}(rhs_c - Rl_c u_{c-2^l} - Rr_c u_{c+2^l}).
 // rhs = y from the R store when w == nullptr, else w ([k][n] FP64).
@@ -161,5 +181,26 @@ cudaError_t launch_refine_gradient(const RefineArgs& a, cudaStream_t st);
 cudaError_t launch_rt_solve(int n, int64_t k, int level, const void* R, double* g, double* w,
                             bool fp32, cudaStream_t st);
 cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t st);
+
+// Kernels of the small-state path (one thread per step / tile / row, element-major layouts),
+// one table per compile-time N.  small_ops(n) is nullptr when n has no table.
+struct SmallOps {
+    int n;
+    cudaError_t (*whiten)(const WhitenArgs&, bool fp32, cudaStream_t);
+    cudaError_t (*level)(int64_t nc, int level, int64_t k, const void* in, void* out, void* R,
+                         double* resid, const double* cn2, const double* cd2,
+                         unsigned long long* bad, bool fp32, cudaStream_t);
+    cudaError_t (*base)(int64_t k, int L, const void* in, void* R, const double* cn2,
+                        const double* cd2, unsigned long long* bad, bool fp32, cudaStream_t);
+    cudaError_t (*backsub)(int64_t k, int level, const void* R, const double* w, double* u,
+                           bool fp32, cudaStream_t);
+    cudaError_t (*selinv)(int64_t k, int level, const void* R, void* Sx, double* Sd,
+                          unsigned long long* bad, bool fp32, cudaStream_t);
+    cudaError_t (*cross)(int64_t k, const void* Sx, double* cross, bool fp32, cudaStream_t);
+    cudaError_t (*rt_solve)(int64_t k, int level, const void* R, double* g, double* w,
+                            bool fp32, cudaStream_t);
+};
+const SmallOps* small_ops(int n);
+constexpr int SMALL_NMAX = 8;
 
 }  // namespace ks

@@ -32,6 +32,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level, int64_t k,
                                                     const T* __restrict__ in, T* __restrict__ out,
                                                     T* __restrict__ R, double* __restrict__ resid,
+                                                    const double* __restrict__ cn2,
+                                                    const double* __restrict__ cd2,
                                                     unsigned long long* bad) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -125,8 +127,8 @@ __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level
             }
             for (int r = tid; r < n; r += nth) {
                 Rj[3 * nn + r] = TOP2[r * L.ld2 + 3 * n];
-                T d = TOP2[r * L.ld2 + r];
-                if (d == T(0) || !isfinite((double)d)) flag_error(bad, ST_SINGULAR, oj);
+                if (diag_is_singular<T>(TOP2[r * L.ld2 + r], cn2[oj * n + r] + cd2[oj * n + r], n))
+                    flag_error(bad, ST_SINGULAR, oj);
             }
             if (j >= 1) {
                 T* En = out + t * CS + nn + n;
@@ -181,8 +183,8 @@ __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level
             }
             for (int r = tid; r < n; r += nth) {
                 Re[3 * nn + r] = TOP2[r * L.ld2 + 2 * n];
-                T d = TOP2[r * L.ld2 + r];
-                if (d == T(0) || !isfinite((double)d)) flag_error(bad, ST_SINGULAR, oe);
+                if (diag_is_singular<T>(TOP2[r * L.ld2 + r], cn2[oe * n + r] + cd2[oe * n + r], n))
+                    flag_error(bad, ST_SINGULAR, oe);
             }
             __syncthreads();
         }
@@ -216,6 +218,7 @@ __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level
 // The last alive column becomes the base block row: Rd = Chat (already triangular), y = rC.
 template <typename T>
 __global__ void base_kernel(int n, int64_t k, int L, const T* __restrict__ in, T* __restrict__ R,
+                            const double* __restrict__ cn2, const double* __restrict__ cd2,
                             unsigned long long* bad) {
     const int64_t c = (1LL << L) - 1;
     const int nn = n * n;
@@ -227,14 +230,14 @@ __global__ void base_kernel(int n, int64_t k, int L, const T* __restrict__ in, T
     }
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
         Rc[3 * nn + r] = in[nn + r];
-        T d = in[r * n + r];
-        if (d == T(0) || !isfinite((double)d)) flag_error(bad, ST_SINGULAR, c);
+        if (diag_is_singular<T>(in[r * n + r], cn2[c * n + r] + cd2[c * n + r], n))
+            flag_error(bad, ST_SINGULAR, c);
     }
 }
 
 cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
-                         void* R, double* resid, unsigned long long* bad, bool fp32,
-                         cudaStream_t st) {
+                         void* R, double* resid, const double* cn2, const double* cd2,
+                         unsigned long long* bad, bool fp32, cudaStream_t st) {
     const int64_t nt = nc / 2;
     if (nt <= 0) return cudaSuccess;
     const TileLayout L = tile_layout(n);
@@ -245,24 +248,24 @@ cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in
         const size_t smem = sizeof(float) * (size_t)L.total;
         cudaFuncSetAttribute(level_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         level_kernel<float><<<blocks, threads, smem, st>>>(n, nc, level, k, (const float*)in,
-                                                            (float*)out, (float*)R, resid, bad);
+                                                            (float*)out, (float*)R, resid, cn2, cd2, bad);
         ++t_launches;
     } else {
         const size_t smem = sizeof(double) * (size_t)L.total;
         cudaFuncSetAttribute(level_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         level_kernel<double><<<blocks, threads, smem, st>>>(n, nc, level, k, (const double*)in,
-                                                             (double*)out, (double*)R, resid, bad);
+                                                             (double*)out, (double*)R, resid, cn2, cd2, bad);
         ++t_launches;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_base(int n, int64_t k, int L, const void* in, void* R,
-                        unsigned long long* bad, bool fp32, cudaStream_t st) {
+cudaError_t launch_base(int n, int64_t k, int L, const void* in, void* R, const double* cn2,
+                        const double* cd2, unsigned long long* bad, bool fp32, cudaStream_t st) {
     if (fp32)
-        base_kernel<float><<<1, 128, 0, st>>>(n, k, L, (const float*)in, (float*)R, bad);
+        base_kernel<float><<<1, 128, 0, st>>>(n, k, L, (const float*)in, (float*)R, cn2, cd2, bad);
     else
-        base_kernel<double><<<1, 128, 0, st>>>(n, k, L, (const double*)in, (double*)R, bad);
+        base_kernel<double><<<1, 128, 0, st>>>(n, k, L, (const double*)in, (double*)R, cn2, cd2, bad);
     ++t_launches;
     return cudaGetLastError();
 }

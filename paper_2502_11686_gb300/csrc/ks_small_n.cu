@@ -1,0 +1,199 @@
+// ks_small_n.cu -- kernels of the small-state path for one compile-time N (the build compiles
+// this file once per N = 1..8 with -DKS_SMALL_N=N).  Each kernel maps one thread to one unit:
+// a step (whitening), a column pair / tail triple (level), a block row (back substitution,
+// SelInv), an alive column (R^T w = g).
+#include "ks_small.cuh"
+
+#ifndef KS_SMALL_N
+#error "compile with -DKS_SMALL_N=<1..8>"
+#endif
+#define KS_CAT2(a, b) a##b
+#define KS_CAT(a, b) KS_CAT2(a, b)
+
+namespace ks {
+namespace small {
+namespace {
+
+constexpr int NN = KS_SMALL_N;
+constexpr int BLK = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(BLK) whiten_k(WhitenArgs a) {
+    const int64_t i = blockIdx.x * (int64_t)BLK + threadIdx.x;
+    if (i < a.k) whiten_step<T, NN>(a, i, reinterpret_cast<T*>(a.level0));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BLK) level_k(int64_t nc, int level, int64_t k, const T* in, T* out,
+                                               T* R, double* resid, const double* cn2,
+                                               const double* cd2, unsigned long long* bad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Stash<T> st{reinterpret_cast<T*>(smem_raw), BLK, (int)threadIdx.x};
+    const int64_t t = blockIdx.x * (int64_t)BLK + threadIdx.x;
+    if (t < (nc >> 1)) level_tile<T, NN>(nc, level, k, t, in, out, R, resid, cn2, cd2, bad, st);
+}
+
+template <typename T>
+__global__ void base_k(int64_t k, int L, const T* in, T* R, const double* cn2, const double* cd2,
+                       unsigned long long* bad) {
+    using D = Dims<NN>;
+    if (threadIdx.x != 0) return;
+    const LevelView<const T, NN> I(in, 1);
+    const RowView<T> RV(R, k, L, D::RS);
+    const int64_t c = (1LL << L) - 1;
+    T Tm[NN][NN];
+    load_upper<T, NN>(I, 0, Tm);
+    check_diag<T, NN>(Tm, cn2, cd2, c, bad);
+    for (int r = 0; r < NN; ++r) {
+        for (int cc = r; cc < NN; ++cc) *RV.at(0, D::ORD + tri(NN, r, cc)) = Tm[r][cc];
+        for (int cc = 0; cc < NN; ++cc) {
+            *RV.at(0, D::ORL + r * NN + cc) = T(0);
+            *RV.at(0, D::ORR + r * NN + cc) = T(0);
+        }
+        *RV.at(0, D::OY + r) = *I.at(0, D::ORC + r);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BLK) backsub_k(int64_t k, int level, const T* R, const double* w,
+                                                 double* u) {
+    const int64_t q = blockIdx.x * (int64_t)BLK + threadIdx.x;
+    if (q < (k >> level) - (k >> (level + 1))) backsub_row<T, NN>(k, level, q, R, w, u);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BLK) selinv_k(int64_t k, int level, const T* R, T* Sx, double* Sd,
+                                                unsigned long long* bad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Stash<T> st{reinterpret_cast<T*>(smem_raw), BLK, (int)threadIdx.x};
+    const int64_t q = blockIdx.x * (int64_t)BLK + threadIdx.x;
+    if (q < (k >> level) - (k >> (level + 1))) selinv_row<T, NN>(k, level, q, R, Sx, Sd, bad, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BLK) cross_k(int64_t k, const T* Sx, double* cross) {
+    using D = Dims<NN>;
+    const int64_t i = blockIdx.x * (int64_t)BLK + threadIdx.x;
+    if (i + 1 >= k) return;
+    const RowView<const T> SV(Sx, k, 0, D::SS);
+    if ((i & 1) == 0) {  // i eliminated at level 0 with right neighbour i+1: Sr_i
+        const int64_t q = i >> 1;
+        for (int e = 0; e < NN * NN; ++e) cross[i * NN * NN + e] = (double)*SV.at(q, NN * NN + e);
+    } else {             // i+1 eliminated at level 0 with left neighbour i: Sl_{i+1}^T
+        const int64_t q = (i + 1) >> 1;
+        for (int r = 0; r < NN; ++r)
+            for (int c = 0; c < NN; ++c)
+                cross[i * NN * NN + r * NN + c] = (double)*SV.at(q, c * NN + r);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BLK) rt_solve_k(int64_t k, int level, const T* R, double* g,
+                                                  double* w) {
+    const int64_t j = blockIdx.x * (int64_t)BLK + threadIdx.x;
+    if (j < (k >> level)) rt_solve_col<T, NN>(k, level, j, R, g, w);
+}
+
+unsigned grid(int64_t work) {
+    int64_t b = (work + BLK - 1) / BLK;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+cudaError_t whiten(const WhitenArgs& a, bool fp32, cudaStream_t st) {
+    if (fp32)
+        whiten_k<float><<<grid(a.k), BLK, 0, st>>>(a);
+    else
+        whiten_k<double><<<grid(a.k), BLK, 0, st>>>(a);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t level(int64_t nc, int lvl, int64_t k, const void* in, void* out, void* R, double* resid,
+                  const double* cn2, const double* cd2, unsigned long long* bad, bool fp32,
+                  cudaStream_t st) {
+    const int64_t nt = nc >> 1;
+    if (nt <= 0) return cudaSuccess;
+    const int stash = TileSlots<NN>::COUNT;
+    if (fp32) {
+        const int smem = stash * BLK * (int)sizeof(float);
+        cudaFuncSetAttribute(level_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        level_k<float><<<grid(nt), BLK, smem, st>>>(nc, lvl, k, (const float*)in, (float*)out,
+                                                   (float*)R, resid, cn2, cd2, bad);
+    } else {
+        const int smem = stash * BLK * (int)sizeof(double);
+        cudaFuncSetAttribute(level_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        level_k<double><<<grid(nt), BLK, smem, st>>>(nc, lvl, k, (const double*)in, (double*)out,
+                                                    (double*)R, resid, cn2, cd2, bad);
+    }
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t base(int64_t k, int L, const void* in, void* R, const double* cn2, const double* cd2,
+                 unsigned long long* bad, bool fp32, cudaStream_t st) {
+    if (fp32)
+        base_k<float><<<1, 32, 0, st>>>(k, L, (const float*)in, (float*)R, cn2, cd2, bad);
+    else
+        base_k<double><<<1, 32, 0, st>>>(k, L, (const double*)in, (double*)R, cn2, cd2, bad);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t backsub(int64_t k, int lvl, const void* R, const double* w, double* u, bool fp32,
+                    cudaStream_t st) {
+    const int64_t rows = (k >> lvl) - (k >> (lvl + 1));
+    if (fp32)
+        backsub_k<float><<<grid(rows), BLK, 0, st>>>(k, lvl, (const float*)R, w, u);
+    else
+        backsub_k<double><<<grid(rows), BLK, 0, st>>>(k, lvl, (const double*)R, w, u);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t selinv(int64_t k, int lvl, const void* R, void* Sx, double* Sd, unsigned long long* bad,
+                   bool fp32, cudaStream_t st) {
+    const int64_t rows = (k >> lvl) - (k >> (lvl + 1));
+    const int stash = SelinvSlots<NN>::COUNT;
+    if (fp32) {
+        const int smem = stash * BLK * (int)sizeof(float);
+        cudaFuncSetAttribute(selinv_k<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        selinv_k<float><<<grid(rows), BLK, smem, st>>>(k, lvl, (const float*)R, (float*)Sx, Sd, bad);
+    } else {
+        const int smem = stash * BLK * (int)sizeof(double);
+        cudaFuncSetAttribute(selinv_k<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        selinv_k<double><<<grid(rows), BLK, smem, st>>>(k, lvl, (const double*)R, (double*)Sx, Sd, bad);
+    }
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t cross(int64_t k, const void* Sx, double* out, bool fp32, cudaStream_t st) {
+    if (k < 2) return cudaSuccess;
+    if (fp32)
+        cross_k<float><<<grid(k - 1), BLK, 0, st>>>(k, (const float*)Sx, out);
+    else
+        cross_k<double><<<grid(k - 1), BLK, 0, st>>>(k, (const double*)Sx, out);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t rt_solve(int64_t k, int lvl, const void* R, double* g, double* w, bool fp32,
+                     cudaStream_t st) {
+    const int64_t cols = k >> lvl;
+    if (fp32)
+        rt_solve_k<float><<<grid(cols), BLK, 0, st>>>(k, lvl, (const float*)R, g, w);
+    else
+        rt_solve_k<double><<<grid(cols), BLK, 0, st>>>(k, lvl, (const double*)R, g, w);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace small
+
+extern const SmallOps KS_CAT(small_ops_, KS_SMALL_N);
+const SmallOps KS_CAT(small_ops_, KS_SMALL_N) = {
+    KS_SMALL_N, small::whiten, small::level, small::base, small::backsub,
+    small::selinv, small::cross, small::rt_solve};
+
+}  // namespace ks

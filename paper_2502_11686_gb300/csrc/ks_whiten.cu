@@ -161,6 +161,20 @@ __global__ void __launch_bounds__(256) whiten_kernel(WhitenArgs a) {
             for (int r = 0; r < mi; ++r) s = fma(Gm[r * L.ldg + n], Gm[r * L.ldg + n], s);
             a.resid[i] = s;
         }
+        // Column norms^2 of U A for state i (Chat_i and B_i) and state i+1 (D_i).
+        for (int col = tid; col < n; col += nth) {
+            double sc = 0.0, sb = 0.0, sd = 0.0;
+            for (int r = 0; r <= col; ++r) sc = fma(Tt[r * L.ldt + col], Tt[r * L.ldt + col], sc);
+            if (hasE) {
+                for (int r = 0; r < n; ++r) {
+                    sb = fma(W[r * L.ldw + col], W[r * L.ldw + col], sb);
+                    sd = fma(W[r * L.ldw + n + col], W[r * L.ldw + n + col], sd);
+                }
+                a.cd2[(i + 1) * n + col] = sd;
+            }
+            a.cn2[i * n + col] = sc + sb;
+            if (i == 0) a.cd2[col] = 0.0;
+        }
         __syncthreads();
     }
 }
