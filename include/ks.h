@@ -151,6 +151,39 @@ const char *ks_last_error(const ks_ctx *ctx);
  * read).  Waits for the ctx's stream so that the phase times are complete. */
 ks_status ks_profile_read(ks_ctx *ctx, ks_profile *out, int reset);
 
+/* Size of the work array that ks_smooth_static uses instead of allocating (16 MiB). */
+#define KS_STATIC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * Smoothing for callers that cannot allocate device memory.  (The paper has no counterpart;
+ * this is a property of the library, not of the method.)
+ *
+ * Some callers are not allowed, or cannot afford, to allocate on the device: a plugin inside a
+ * host application that owns the whole device-memory budget, or a real-time loop that must
+ * never wait on the allocator (cudaMalloc can block, cudaFree synchronizes the device).  This
+ * entry point needs no ks_ctx and calls no allocating routine.  The caller passes the inputs and
+ * outputs; all other work memory comes from one array of KS_STATIC_SCRATCH_BYTES bytes built
+ * into libks.so, which every GPU that loads the library keeps until the process exits.
+ *
+ * Same arguments and layouts as ks_smooth, restricted to: FP64; 1 <= n <= 8; the same
+ * observation count m (0 <= m <= n) at every step; every array a DEVICE pointer of `device`;
+ * (k, n, covariances or not) small enough for the array -- otherwise KS_ERR_ARG and a message
+ * in err.  cov_out (NULL = states only) receives [k][n][n] covariances.  err / err_len: a
+ * caller buffer for the message of a failure (may be NULL).  Runs on `stream` (a
+ * cudaStream_t, NULL = the legacy default stream), waits for its work, reports device-detected
+ * errors like ks_smooth, and leaves the caller's current device unchanged.
+ *
+ * The first call on each device looks up that device's address of the built-in array and keeps
+ * it; make that first call before any stream capture.  All calls share the one array and each
+ * call overwrites what the previous one left there: calls that overlap on the GPU (other
+ * streams, other host threads) race, so the caller must serialize them.
+ */
+ks_status ks_smooth_static(int device, void *stream, int64_t k, int n, int m,
+                           const double *F, const double *H, const double *c, const double *K,
+                           const double *G, const double *o, const double *C,
+                           double *u_out, double *cov_out, int64_t *info,
+                           char *err, size_t err_len);
+
 /* Largest state dimension n this ctx's precision supports on its device. */
 int ks_max_n(const ks_ctx *ctx);
 

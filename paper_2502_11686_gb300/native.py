@@ -22,7 +22,7 @@ KS_FP64, KS_FP32_REFINE = 0, 1
 # Every symbol include/ks.h declares.
 EXPORTS = ("ks_default_options", "ks_create", "ks_smooth", "ks_covariances", "ks_residual",
            "ks_release", "ks_sync", "ks_destroy", "ks_last_error", "ks_max_n", "ks_max_m",
-           "ks_profile_read")
+           "ks_profile_read", "ks_smooth_static")
 PHASES = ("whiten", "level", "backsub", "refine", "selinv", "copy")
 
 
@@ -85,6 +85,9 @@ def load():
         lib.ks_max_m.restype = I
         lib.ks_profile_read.argtypes = [P, ctypes.POINTER(ks_profile), I]
         lib.ks_profile_read.restype = I
+        lib.ks_smooth_static.argtypes = [I, P, I64, I, I, P, P, P, P, P, P, P, P, P,
+                                         ctypes.POINTER(I64), ctypes.c_char_p, ctypes.c_size_t]
+        lib.ks_smooth_static.restype = I
         _lib = lib
         return lib
 
@@ -182,3 +185,14 @@ def ks_profile_read(ctx, reset=False) -> dict:
     return {"launches": int(pr.launches), "calls": int(pr.calls),
             "phase_launches": {PHASES[i]: int(pr.phase_launches[i]) for i in range(6)},
             "phase_ms": {PHASES[i]: float(pr.phase_ms[i]) for i in range(6)}}
+
+
+def ks_smooth_static(device, stream, k, n, m, F, H, c, K, G, o, C, u_out, cov_out=None):
+    """The allocation-free entry point (device arrays only; see include/ks.h).
+    Returns (status, info, message); never raises for a library status."""
+    info = ctypes.c_int64(-1)
+    buf = ctypes.create_string_buffer(512)
+    st = load().ks_smooth_static(int(device), stream, int(k), int(n), int(m), ptr(F), ptr(H),
+                                 ptr(c), ptr(K), ptr(G), ptr(o), ptr(C), ptr(u_out),
+                                 ptr(cov_out), ctypes.byref(info), buf, len(buf))
+    return st, info.value, buf.value.decode()
