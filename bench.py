@@ -36,12 +36,13 @@ FP32_PEAK_TFLOPS = 80.5      # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 WORKLOADS = {
     "long_k1e6_n6": dict(k=1_000_000, n=6, m=6, f_scale=0.99, sample_k=1_000_000,
+                         ref_sample_k=100_000,
                          desc="k=1,000,000 states, n=m=6, F=0.99*orth, H=I, G~N(0,1/6), "
                               "K,C=LL^T per step; states + all covariances"),
-    "cv_k1000_n4": dict(k=1000, n=4, m=2, cv=True, sample_k=1000,
+    "cv_k1000_n4": dict(k=1000, n=4, m=2, cv=True, sample_k=1000, ref_sample_k=1000,
                         desc="k=1000, 2-D constant velocity n=4, m=2, G~N(0,1), K=0.01I, "
                              "C=0.25I; states + all covariances"),
-    "dense_k1e5_n48": dict(k=100_000, n=48, m=48, f_scale=0.995, sample_k=1500,
+    "dense_k1e5_n48": dict(k=100_000, n=48, m=48, f_scale=0.995, sample_k=1500, ref_sample_k=300,
                            desc="k=100,000 states, n=m=48, F=0.995*orth, H=I, G~N(0,1/48), "
                                 "K,C=LL^T per step; states + all covariances"),
 }
@@ -56,18 +57,44 @@ def make_problem(wl, seed, k=None):
 
 
 def flops_per_step(n, m, precision):
-    """Algorithmic flops per smoothed step of each phase (the structured Householder scheme:
-    a reflector touches the p+1 rows of one triangular-over-full pair)."""
-    def tpqrt(p, comps):  # n reflectors, each applied to the trailing factor columns + comps
-        return 2 * p * n * (n - 1) + 4 * p * n * comps
-    whiten = (n ** 3 + m ** 3) / 3 + n * n * (2 * n + 1) + m * m * (n + 1) + tpqrt(m, 1)
-    level = tpqrt(n, n + 1) + tpqrt(n, 2 * n + 1) + tpqrt(n, 1)
+    """Algorithmic flops per smoothed step of each phase, counted as the kernels perform them
+    (an FMA is 2 flops; a divide or square root 1).  The Householder steps use the structured
+    "triangle over full block" reflectors: a reflector touches one row of the triangle and the
+    p rows of the full block."""
+    def factor(p):      # QR of [T (n x n upper) ; M (p x n)]
+        return 2 * p * n * (n - 1) + 3 * p * n + 4 * n
+    def apply(p, cols):  # n reflectors applied to `cols` companion columns
+        return cols * n * (4 * p + 2)
+    tri = n * (n + 1) // 2
+    whiten = (n ** 3 + m ** 3) / 3 + (2 * n + 1) * n * n + n * m * m + m * m \
+        + factor(m) + apply(m, 1)
+    level = 3 * factor(n) + apply(n, n + 1) + apply(n, 2 * n + 1) + apply(n, 1)
     backsub = 5 * n * n
-    selinv = 3 * n ** 3 + 8 * n ** 3 + 6 * n ** 3
-    refine = (4 * n * n + 2 * n * n) + (2 * n * m + m * m * 2 + 2 * n * m) + 5 * n * n + 5 * n * n \
-        if precision == "fp32_refine" else 0
+    ri = 2 * sum(c - i for c in range(n) for i in range(c + 1)) + tri
+    selinv = ri + 2 * 2 * n * tri + 2 * sum((j + 1) * (n - j) for j in range(n)) \
+        + 2 * 2 * n * (2 * n * n + tri)
+    refine = (20 * n * n + 4 * m * n + 2 * m * m + n) if precision == "fp32_refine" else 0
     return {"whiten": whiten, "level": level, "backsub": backsub, "selinv": selinv,
             "refine": refine}
+
+
+def measured_traffic(phase, precision, n):
+    """DRAM bytes per unit from a committed ncu capture, if the kernel source still matches."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    key = f"{phase} phase {precision} n={n}"
+    r = rec.get(key)
+    if not r:
+        return None
+    csrc = os.path.join(ROOT, "paper_2502_11686_gb300", "csrc")
+    src = open(os.path.join(csrc, "ks_small.cuh"), "rb").read() + \
+        open(os.path.join(csrc, "ks_small_n.cu"), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != r["source_digest"]:
+        return None
+    return r
 
 
 def bytes_per_step(n, m, precision):
@@ -160,7 +187,7 @@ def reference_arm(args, wl):
     if rank != 0:
         return 0
     import oracle
-    p = make_problem(wl, seed=0, k=wl["sample_k"])
+    p = make_problem(wl, seed=0, k=wl["ref_sample_k"])
     oracle.smooth(p)
     for _ in range(args.warmup):
         oracle.smooth(p, covariances=True)
@@ -193,8 +220,15 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_refine"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--k", type=int, default=None,
+                    help="override the number of states (smaller cases for profiling)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.k:
+        wl["k"] = args.k
+        wl["sample_k"] = min(wl["sample_k"], args.k)
+        wl["ref_sample_k"] = min(wl["ref_sample_k"], args.k)
+        wl["desc"] = wl["desc"].replace(f"k={WORKLOADS[args.workload]['k']:,}", f"k={args.k:,}")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -323,6 +357,13 @@ def main():
             "flops_per_step": fl[top], "hbm_bytes_per_step": by[top],
             "achieved_hbm_gbs": by[top] * k / (phase_ms[top] / 1e3) / 1e9,
             "traffic": None}
+    tr = measured_traffic(top, args.precision, n)
+    if tr is not None and top == "level":
+        launches = max(1, prof["phase_launches"]["level"] // args.steps)
+        roof["traffic"] = tr["dram_bytes_per_tile"] * (k - 1) / launches
+        roof["traffic_unit"] = "bytes per launch (average over the level launches of a pass)"
+        roof["traffic_source"] = tr["capture"]
+        roof["algorithmic_bytes_per_launch"] = by[top] * k / launches
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         rate, sample = oracle_rate(wl)

@@ -482,12 +482,15 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
         ra.q = (double*)(ws + o_q);
         double* w = (double*)(ws + o_w);
         double* d = (double*)(ws + o_d);
-        KS_CUDA(ctx, launch_refine_gradient(ra, st));
-        for (int l = 0; l <= L; ++l)
-            KS_CUDA(ctx, sops ? sops->rt_solve(k, l, R, ra.g, w, fp32, st) : launch_rt_solve(n, k, l, R, ra.g, w, fp32, st));
-        for (int l = L; l >= 0; --l)
-            KS_CUDA(ctx, sops ? sops->backsub(k, l, R, w, d, fp32, st) : launch_backsub(n, k, l, R, w, d, fp32, st));
-        KS_CUDA(ctx, launch_axpy(u, d, k * n, st));
+        if (sops) {
+            // FP32 correction solve; the scratch vectors reuse the FP64 ones' space.
+            KS_CUDA(ctx, sops->refine(ra, (float*)ra.q, (float*)ra.g, (float*)w, (float*)d, R, L, st));
+        } else {
+            KS_CUDA(ctx, launch_refine_gradient(ra, st));
+            for (int l = 0; l <= L; ++l) KS_CUDA(ctx, launch_rt_solve(n, k, l, R, ra.g, w, fp32, st));
+            for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_backsub(n, k, l, R, w, d, fp32, st));
+            KS_CUDA(ctx, launch_axpy(u, d, k * n, st));
+        }
     }
     if (!u_dev) {
         Phase ph(ctx, KS_PHASE_COPY);

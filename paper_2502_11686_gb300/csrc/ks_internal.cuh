@@ -102,6 +102,81 @@ __host__ __device__ inline SelinvLayout selinv_layout(int n) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Record access policies of the column-owner kernels.  AosIO: the generic layout (records per
+// column, R / S rows by original state index).  SoaIO: the element-major layout of the
+// small-state path (even / odd column planes, packed upper triangles, R / S rows per level), so
+// that the column-owner kernels can also run the top levels of a small-state problem, where a
+// level has too few tiles for one thread per tile.
+template <typename T>
+struct AosIO {
+    int n;
+    int64_t CS, RS;
+    const T* in;
+    T* out;
+    T* R;
+    __device__ AosIO(int n_, int64_t, int, int64_t, const T* i, T* o, T* r)
+        : n(n_), CS(level_cs(n_)), RS(rstore_rs(n_)), in(i), out(o), R(r) {}
+    __device__ T C(int64_t j, int r, int c) const { return in[j * CS + r * n + c]; }
+    __device__ T RC(int64_t j, int r) const { return in[j * CS + n * n + r]; }
+    __device__ T E(int64_t j, int r, int c2) const { return in[j * CS + n * n + n + r * 2 * n + c2]; }
+    __device__ T RE(int64_t j, int r) const { return in[j * CS + 3 * n * n + n + r]; }
+    __device__ void setC(int64_t t, int r, int c, T v) const { out[t * CS + r * n + c] = c >= r ? v : T(0); }
+    __device__ void setRC(int64_t t, int r, T v) const { out[t * CS + n * n + r] = v; }
+    __device__ void setE(int64_t t, int r, int c2, T v) const { out[t * CS + n * n + n + r * 2 * n + c2] = v; }
+    __device__ void setRE(int64_t t, int r, T v) const { out[t * CS + 3 * n * n + n + r] = v; }
+    // Block row of the column with level row q and original index oc; part 0/1/2 = Rd/Rl/Rr.
+    __device__ void setR(int64_t, int64_t oc, int part, int r, int c, T v) const {
+        R[oc * RS + part * n * n + r * n + c] = v;
+    }
+    __device__ void setY(int64_t, int64_t oc, int r, T v) const { R[oc * RS + 3 * n * n + r] = v; }
+};
+
+template <typename T>
+struct SoaIO {
+    int n, nt, CS, RS;
+    int64_t nE, nO, nE2, nO2, rows, roff;
+    const T* in;
+    T* out;
+    T* R;
+    __device__ SoaIO(int n_, int64_t nc, int level, int64_t k, const T* i, T* o, T* r)
+        : n(n_), nt(n_ * (n_ + 1) / 2), in(i), out(o), R(r) {
+        CS = nt + 2 * n + 2 * n * n;
+        RS = nt + 2 * n * n + n;
+        nE = (nc + 1) >> 1;
+        nO = nc >> 1;
+        nE2 = ((nc >> 1) + 1) >> 1;
+        nO2 = (nc >> 1) >> 1;
+        rows = (k >> level) - (k >> (level + 1));
+        roff = (k - (k >> level)) * (int64_t)RS;
+    }
+    __device__ int tri(int r, int c) const { return r * n - r * (r - 1) / 2 + (c - r); }
+    __device__ T ie(int64_t j, int e) const {
+        return (j & 1) ? in[(int64_t)CS * nE + (int64_t)e * nO + (j >> 1)] : in[(int64_t)e * nE + (j >> 1)];
+    }
+    __device__ T* oe(int64_t t, int e) const {
+        return (t & 1) ? out + (int64_t)CS * nE2 + (int64_t)e * nO2 + (t >> 1) : out + (int64_t)e * nE2 + (t >> 1);
+    }
+    __device__ T C(int64_t j, int r, int c) const { return c >= r ? ie(j, tri(r, c)) : T(0); }
+    __device__ T RC(int64_t j, int r) const { return ie(j, nt + r); }
+    __device__ T E(int64_t j, int r, int c2) const { return ie(j, nt + n + r * 2 * n + c2); }
+    __device__ T RE(int64_t j, int r) const { return ie(j, nt + n + 2 * n * n + r); }
+    __device__ void setC(int64_t t, int r, int c, T v) const { if (c >= r) *oe(t, tri(r, c)) = v; }
+    __device__ void setRC(int64_t t, int r, T v) const { *oe(t, nt + r) = v; }
+    __device__ void setE(int64_t t, int r, int c2, T v) const { *oe(t, nt + n + r * 2 * n + c2) = v; }
+    __device__ void setRE(int64_t t, int r, T v) const { *oe(t, nt + n + 2 * n * n + r) = v; }
+    __device__ void setR(int64_t q, int64_t, int part, int r, int c, T v) const {
+        if (part == 0) {
+            if (c >= r) R[roff + (int64_t)tri(r, c) * rows + q] = v;
+        } else {
+            R[roff + (int64_t)(nt + (part - 1) * n * n + r * n + c) * rows + q] = v;
+        }
+    }
+    __device__ void setY(int64_t q, int64_t, int r, T v) const {
+        R[roff + (int64_t)(nt + 2 * n * n + r) * rows + q] = v;
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
 // Launch wrappers (defined in the .cu files).  All return cudaGetLastError() of the launch and
 // add the number of kernels they launched to t_launches (the calling thread's counter).
 extern thread_local uint64_t t_launches;
@@ -145,6 +220,14 @@ cudaError_t launch_whiten(const WhitenArgs& a, bool fp32, cudaStream_t st);
 cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
                          void* R, double* resid, const double* cn2, const double* cd2,
                          unsigned long long* bad, bool fp32, cudaStream_t st);
+
+// The column-owner level kernel on the small-state layout (top levels of a small problem).
+cudaError_t launch_level_soa(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
+                             void* R, double* resid, const double* cn2, const double* cd2,
+                             unsigned long long* bad, bool fp32, cudaStream_t st);
+// The column-owner SelInv kernel on the small-state layout.
+cudaError_t launch_selinv_soa(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
+                              unsigned long long* bad, bool fp32, cudaStream_t st);
 
 cudaError_t launch_base(int n, int64_t k, int L, const void* in, void* R, const double* cn2,
                         const double* cd2, unsigned long long* bad, bool fp32, cudaStream_t st);
@@ -197,8 +280,9 @@ struct SmallOps {
     cudaError_t (*selinv)(int64_t k, int level, const void* R, void* Sx, double* Sd,
                           unsigned long long* bad, bool fp32, cudaStream_t);
     cudaError_t (*cross)(int64_t k, const void* Sx, double* cross, bool fp32, cudaStream_t);
-    cudaError_t (*rt_solve)(int64_t k, int level, const void* R, double* g, double* w,
-                            bool fp32, cudaStream_t);
+    // Refinement (FP32 mode only): q, g from FP64 residuals; R^T w = g; R d = w; u += d.
+    cudaError_t (*refine)(const RefineArgs& a, float* q, float* g, float* w, float* d,
+                          const void* R, int L, cudaStream_t);
 };
 const SmallOps* small_ops(int n);
 constexpr int SMALL_NMAX = 8;

@@ -28,7 +28,7 @@
 
 namespace ks {
 
-template <typename T>
+template <typename T, typename IO>
 __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level, int64_t k,
                                                     const T* __restrict__ in, T* __restrict__ out,
                                                     T* __restrict__ R, double* __restrict__ resid,
@@ -45,49 +45,45 @@ __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level
     T* BOT3 = sm + L.bot3;
     T* scal = sm + L.scal;
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int64_t CS = level_cs(n), RS = rstore_rs(n);
     const int nn = n * n;
     const int64_t nt = nc / 2;
+    const IO io(n, nc, level, k, in, out, R);
 
     for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
         const int64_t j = 2 * t, s = j + 1;
         const bool triple = (nc & 1) && (t == nt - 1);
-        const T* cj = in + j * CS;
-        const T* cs = in + s * CS;
         const int64_t oj = ((j + 1) << level) - 1;  // original index of column j
 
         // ---- loads ----
         for (int e = tid; e < n * L.ld2; e += nth) {
             int r = e / L.ld2, c = e - r * L.ld2;
             T v = T(0);
-            if (c < n) v = cj[r * n + c];
-            else if (c == 3 * n) v = cj[nn + r];
+            if (c < n) v = io.C(j, r, c);
+            else if (c == 3 * n) v = io.RC(j, r);
             TOP2[e] = v;
         }
         if (j >= 1) {
-            const T* Ej = cj + nn + n;
             for (int e = tid; e < n * L.ld2; e += nth) {
                 int r = e / L.ld2, c = e - r * L.ld2;
                 T v = T(0);
-                if (c < n) v = Ej[r * 2 * n + n + c];              // D_j (factor bottom)
-                else if (c < 2 * n) v = Ej[r * 2 * n + (c - n)];   // -B_j (left companion)
-                else if (c == 3 * n) v = Ej[2 * nn + r];           // rE_j
+                if (c < n) v = io.E(j, r, n + c);                  // D_j (factor bottom)
+                else if (c < 2 * n) v = io.E(j, r, c - n);         // -B_j (left companion)
+                else if (c == 3 * n) v = io.RE(j, r);              // rE_j
                 BOT2[e] = v;
             }
         }
         {
-            const T* Es = cs + nn + n;
             for (int e = tid; e < nn; e += nth) {
                 int r = e / n, c = e - r * n;
-                BF[r * L.ldf + c] = Es[r * 2 * n + c];              // -B_s
-                BOT3[r * L.ld3 + c] = Es[r * 2 * n + n + c];        // D_s
+                BF[r * L.ldf + c] = io.E(s, r, c);                  // -B_s
+                BOT3[r * L.ld3 + c] = io.E(s, r, n + c);            // D_s
             }
-            for (int r = tid; r < n; r += nth) BOT3[r * L.ld3 + n] = Es[2 * nn + r];  // rE_s
+            for (int r = tid; r < n; r += nth) BOT3[r * L.ld3 + n] = io.RE(s, r);    // rE_s
             for (int e = tid; e < nn; e += nth) {
                 int r = e / n, c = e - r * n;
-                TOP3[r * L.ld3 + c] = cs[e];                        // Chat_s
+                TOP3[r * L.ld3 + c] = io.C(s, r, c);                // Chat_s
             }
-            for (int r = tid; r < n; r += nth) TOP3[r * L.ld3 + n] = cs[nn + r];      // rC_s
+            for (int r = tid; r < n; r += nth) TOP3[r * L.ld3 + n] = io.RC(s, r);    // rC_s
         }
         __syncthreads();
 
@@ -118,25 +114,23 @@ __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level
         }
         // ---- block row j of R, and the reduced coupling row of new column t ----
         {
-            T* Rj = R + oj * RS;
             for (int e = tid; e < nn; e += nth) {
                 int r = e / n, c = e - r * n;
-                Rj[e] = TOP2[r * L.ld2 + c];
-                Rj[nn + e] = (j >= 1) ? TOP2[r * L.ld2 + n + c] : T(0);
-                Rj[2 * nn + e] = TOP2[r * L.ld2 + 2 * n + c];
+                io.setR(t, oj, 0, r, c, c >= r ? TOP2[r * L.ld2 + c] : T(0));
+                io.setR(t, oj, 1, r, c, (j >= 1) ? TOP2[r * L.ld2 + n + c] : T(0));
+                io.setR(t, oj, 2, r, c, TOP2[r * L.ld2 + 2 * n + c]);
             }
             for (int r = tid; r < n; r += nth) {
-                Rj[3 * nn + r] = TOP2[r * L.ld2 + 3 * n];
+                io.setY(t, oj, r, TOP2[r * L.ld2 + 3 * n]);
                 if (diag_is_singular<T>(TOP2[r * L.ld2 + r], cn2[oj * n + r] + cd2[oj * n + r], n))
                     flag_error(bad, ST_SINGULAR, oj);
             }
             if (j >= 1) {
-                T* En = out + t * CS + nn + n;
                 for (int e = tid; e < 2 * nn; e += nth) {
                     int r = e / (2 * n), c = e - r * 2 * n;
-                    En[e] = BOT2[r * L.ld2 + n + c];
+                    io.setE(t, r, c, BOT2[r * L.ld2 + n + c]);
                 }
-                for (int r = tid; r < n; r += nth) En[2 * nn + r] = BOT2[r * L.ld2 + 3 * n];
+                for (int r = tid; r < n; r += nth) io.setRE(t, r, BOT2[r * L.ld2 + 3 * n]);
             }
         }
         __syncthreads();
@@ -144,22 +138,20 @@ __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level
         // ---- tail: step 2 of column e (no right neighbour), reusing TOP2 / BF ----
         if (triple) {
             const int64_t e_ = j + 2;
-            const T* ce = in + e_ * CS;
-            const T* Ee = ce + nn + n;
             const int64_t oe = ((e_ + 1) << level) - 1;
             for (int e = tid; e < n * L.ld2; e += nth) {
                 int r = e / L.ld2, c = e - r * L.ld2;
                 T v = T(0);
-                if (c < n) v = ce[r * n + c];
-                else if (c == 2 * n) v = ce[nn + r];
+                if (c < n) v = io.C(e_, r, c);
+                else if (c == 2 * n) v = io.RC(e_, r);
                 TOP2[e] = v;
             }
             for (int e = tid; e < nn; e += nth) {
                 int r = e / n, c = e - r * n;
-                BF[r * L.ldf + c] = Ee[r * 2 * n + n + c];              // D_e
-                BOT3[(n + r) * L.ld3 + c] = Ee[r * 2 * n + c];          // -B_e -> Z_e
+                BF[r * L.ldf + c] = io.E(e_, r, n + c);                 // D_e
+                BOT3[(n + r) * L.ld3 + c] = io.E(e_, r, c);             // -B_e -> Z_e
             }
-            for (int r = tid; r < n; r += nth) BOT3[(n + r) * L.ld3 + n] = Ee[2 * nn + r];
+            for (int r = tid; r < n; r += nth) BOT3[(n + r) * L.ld3 + n] = io.RE(e_, r);
             __syncthreads();
             {
                 const int fcol = tid < n ? tid : -1;
@@ -174,15 +166,14 @@ __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level
                 }
                 tpqrt_columns<T>(n, n, TOP2, L.ld2, BF, L.ldf, fcol, ctop, L.ld2, cbot, L.ld3, scal);
             }
-            T* Re = R + oe * RS;
             for (int e = tid; e < nn; e += nth) {
                 int r = e / n, c = e - r * n;
-                Re[e] = TOP2[r * L.ld2 + c];
-                Re[nn + e] = TOP2[r * L.ld2 + n + c];
-                Re[2 * nn + e] = T(0);
+                io.setR(t + 1, oe, 0, r, c, c >= r ? TOP2[r * L.ld2 + c] : T(0));
+                io.setR(t + 1, oe, 1, r, c, TOP2[r * L.ld2 + n + c]);
+                io.setR(t + 1, oe, 2, r, c, T(0));
             }
             for (int r = tid; r < n; r += nth) {
-                Re[3 * nn + r] = TOP2[r * L.ld2 + 2 * n];
+                io.setY(t + 1, oe, r, TOP2[r * L.ld2 + 2 * n]);
                 if (diag_is_singular<T>(TOP2[r * L.ld2 + r], cn2[oe * n + r] + cd2[oe * n + r], n))
                     flag_error(bad, ST_SINGULAR, oe);
             }
@@ -196,12 +187,11 @@ __global__ void __launch_bounds__(256) level_kernel(int n, int64_t nc, int level
             T* ctop = (tid == n) ? TOP3 + n : nullptr;
             T* cbot = (tid == n) ? BOT3 + n : nullptr;
             tpqrt_columns<T>(n, p3, TOP3, L.ld3, BOT3, L.ld3, fcol, ctop, L.ld3, cbot, L.ld3, scal);
-            T* Cn = out + t * CS;
             for (int e = tid; e < nn; e += nth) {
                 int r = e / n, c = e - r * n;
-                Cn[e] = c >= r ? TOP3[r * L.ld3 + c] : T(0);
+                io.setC(t, r, c, TOP3[r * L.ld3 + c]);
             }
-            for (int r = tid; r < n; r += nth) Cn[nn + r] = TOP3[r * L.ld3 + n];
+            for (int r = tid; r < n; r += nth) io.setRC(t, r, TOP3[r * L.ld3 + n]);
             if (tid == 0) {
                 double acc = 0.0;
                 for (int r = 0; r < p3; ++r) {
@@ -235,9 +225,11 @@ __global__ void base_kernel(int n, int64_t k, int L, const T* __restrict__ in, T
     }
 }
 
-cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
-                         void* R, double* resid, const double* cn2, const double* cd2,
-                         unsigned long long* bad, bool fp32, cudaStream_t st) {
+template <template <typename> class IO>
+static cudaError_t launch_level_io(int n, int64_t nc, int level, int64_t k, const void* in,
+                                   void* out, void* R, double* resid, const double* cn2,
+                                   const double* cd2, unsigned long long* bad, bool fp32,
+                                   cudaStream_t st) {
     const int64_t nt = nc / 2;
     if (nt <= 0) return cudaSuccess;
     const TileLayout L = tile_layout(n);
@@ -246,18 +238,29 @@ cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in
     const unsigned blocks = (unsigned)(nt < (1LL << 30) ? nt : (1LL << 30));
     if (fp32) {
         const size_t smem = sizeof(float) * (size_t)L.total;
-        cudaFuncSetAttribute(level_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        level_kernel<float><<<blocks, threads, smem, st>>>(n, nc, level, k, (const float*)in,
-                                                            (float*)out, (float*)R, resid, cn2, cd2, bad);
-        ++t_launches;
+        cudaFuncSetAttribute(level_kernel<float, IO<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        level_kernel<float, IO<float>><<<blocks, threads, smem, st>>>(
+            n, nc, level, k, (const float*)in, (float*)out, (float*)R, resid, cn2, cd2, bad);
     } else {
         const size_t smem = sizeof(double) * (size_t)L.total;
-        cudaFuncSetAttribute(level_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        level_kernel<double><<<blocks, threads, smem, st>>>(n, nc, level, k, (const double*)in,
-                                                             (double*)out, (double*)R, resid, cn2, cd2, bad);
-        ++t_launches;
+        cudaFuncSetAttribute(level_kernel<double, IO<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        level_kernel<double, IO<double>><<<blocks, threads, smem, st>>>(
+            n, nc, level, k, (const double*)in, (double*)out, (double*)R, resid, cn2, cd2, bad);
     }
+    ++t_launches;
     return cudaGetLastError();
+}
+
+cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
+                         void* R, double* resid, const double* cn2, const double* cd2,
+                         unsigned long long* bad, bool fp32, cudaStream_t st) {
+    return launch_level_io<AosIO>(n, nc, level, k, in, out, R, resid, cn2, cd2, bad, fp32, st);
+}
+
+cudaError_t launch_level_soa(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
+                             void* R, double* resid, const double* cn2, const double* cd2,
+                             unsigned long long* bad, bool fp32, cudaStream_t st) {
+    return launch_level_io<SoaIO>(n, nc, level, k, in, out, R, resid, cn2, cd2, bad, fp32, st);
 }
 
 cudaError_t launch_base(int n, int64_t k, int L, const void* in, void* R, const double* cn2,

@@ -764,12 +764,147 @@ __device__ void selinv_row(int64_t k, int level, int64_t q, const T* R, T* Sx, d
     if (neg) flag_error(bad, ST_SINGULAR, c);
 }
 
-// ---- R^T w = g at one level for one alive column (refinement) ------------------------------
-template <typename TR, int N>
-__device__ void rt_solve_col(int64_t k, int level, int64_t jj, const TR* R, double* g, double* w) {
+// ---- refinement (KS_FP32_REFINE) -----------------------------------------------------------
+// Mixed-precision iterative refinement: only the residuals -- differences of nearly equal
+// quantities -- are formed in FP64; the correction solve R^T R d = g runs in FP32 with the
+// FP32 R, like the factorization itself.
+
+// q_i = K_i^{-1} e_i with e_i = F_i u_i + c_i - H_i u_{i+1} (e in FP64, the solve in FP32).
+template <int N>
+__device__ void refine_q_step(const RefineArgs& a, int64_t i, float* q) {
+    const double* F = a.F + i * N * N;
+    const double* H = a.H + i * N * N;
+    const double* Lk = a.LK + i * N * N;
+    double u0[N], u1[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        u0[p] = a.u[i * N + p];
+        u1[p] = a.u[(i + 1) * N + p];
+    }
+    float e[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        double s = a.c ? a.c[i * N + r] : 0.0;
+#pragma unroll
+        for (int p = 0; p < N; ++p) s = fma(F[r * N + p], u0[p], s);
+#pragma unroll
+        for (int p = 0; p < N; ++p) s = fma(-H[r * N + p], u1[p], s);
+        e[r] = (float)s;
+    }
+    float L[N][N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) L[r][c] = (float)Lk[r * N + c];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+        float s = e[r];
+#pragma unroll
+        for (int p = 0; p < r; ++p) s = fmaf(-L[r][p], e[p], s);
+        e[r] = s / L[r][r];
+    }
+#pragma unroll
+    for (int r = N - 1; r >= 0; --r) {
+        float s = e[r];
+#pragma unroll
+        for (int p = r + 1; p < N; ++p) s = fmaf(-L[p][r], e[p], s);
+        e[r] = s / L[r][r];
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r) q[i * N + r] = e[r];
+}
+
+// g_c = H_{c-1}^T q_{c-1} - F_c^T q_c + G_c^T C_c^{-1} (o_c - G_c u_c); o - G u in FP64.
+template <int N>
+__device__ void refine_g_col(const RefineArgs& a, int64_t c, const float* q, float* g) {
+    float acc[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) acc[r] = 0.f;
+    if (c >= 1) {
+        const double* H = a.H + (c - 1) * N * N;
+        float qv[N];
+#pragma unroll
+        for (int p = 0; p < N; ++p) qv[p] = q[(c - 1) * N + p];
+#pragma unroll
+        for (int p = 0; p < N; ++p)
+#pragma unroll
+            for (int r = 0; r < N; ++r) acc[r] = fmaf((float)H[p * N + r], qv[p], acc[r]);
+    }
+    if (c + 1 < a.k) {
+        const double* F = a.F + c * N * N;
+        float qv[N];
+#pragma unroll
+        for (int p = 0; p < N; ++p) qv[p] = q[c * N + p];
+#pragma unroll
+        for (int p = 0; p < N; ++p)
+#pragma unroll
+            for (int r = 0; r < N; ++r) acc[r] = fmaf(-(float)F[p * N + r], qv[p], acc[r]);
+    }
+    int mi;
+    int64_t go, co;
+    if (a.m_uniform >= 0) {
+        mi = a.m_uniform;
+        go = c * mi;
+        co = c * (int64_t)mi * mi;
+    } else {
+        mi = a.m[c];
+        go = a.goff[c];
+        co = a.coff[c];
+    }
+    if (mi > 0) {
+        const double* G = a.G + go * N;
+        const double* Lc = a.LC + co;
+        double uc[N];
+#pragma unroll
+        for (int p = 0; p < N; ++p) uc[p] = a.u[c * N + p];
+        float v[N];
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            if (r < mi) {
+                double s = a.o[go + r];
+#pragma unroll
+                for (int p = 0; p < N; ++p) s = fma(-G[r * N + p], uc[p], s);
+                v[r] = (float)s;
+            } else {
+                v[r] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            if (r < mi) {
+                float s = v[r];
+#pragma unroll
+                for (int p = 0; p < r; ++p) s = fmaf(-(float)Lc[r * mi + p], v[p], s);
+                v[r] = s / (float)Lc[r * mi + r];
+            }
+        }
+#pragma unroll
+        for (int r = N - 1; r >= 0; --r) {
+            if (r < mi) {
+                float s = v[r];
+#pragma unroll
+                for (int p = r + 1; p < N; ++p)
+                    if (p < mi) s = fmaf(-(float)Lc[p * mi + r], v[p], s);
+                v[r] = s / (float)Lc[r * mi + r];
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < N; ++p)
+            if (p < mi)
+#pragma unroll
+                for (int r = 0; r < N; ++r) acc[r] = fmaf((float)G[p * N + r], v[p], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r) g[c * N + r] = acc[r];
+}
+
+// R^T w = g at one level for one alive column: pull the blocks of the rows eliminated at
+// level-1 that touch column c, then, if c is eliminated at this level, solve Rd^T w_c = g_c.
+template <typename TR, typename TV, int N>
+__device__ void rt_solve_col(int64_t k, int level, int64_t jj, const TR* R, TV* g, TV* w) {
     using D = Dims<N>;
     const int64_t c = ((jj + 1) << level) - 1;
-    double r[N];
+    TV r[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) r[i] = g[c * N + i];
     if (level >= 1) {
@@ -777,19 +912,23 @@ __device__ void rt_solve_col(int64_t k, int level, int64_t jj, const TR* R, doub
         const int64_t h = 1LL << (level - 1);
         if (c - h >= 0) {  // row c-h: its right block Rr sits in column c
             const int64_t qq = (c - h + 1) >> level;
-            const double* wr = w + (c - h) * N;
+            TV wr[N];
+#pragma unroll
+            for (int p = 0; p < N; ++p) wr[p] = w[(c - h) * N + p];
 #pragma unroll
             for (int i = 0; i < N; ++i)
 #pragma unroll
-                for (int p = 0; p < N; ++p) r[i] = fma(-(double)*RP.at(qq, D::ORR + p * N + i), wr[p], r[i]);
+                for (int p = 0; p < N; ++p) r[i] = fma(-(TV)*RP.at(qq, D::ORR + p * N + i), wr[p], r[i]);
         }
         if (c + h < k) {  // row c+h: its left block Rl sits in column c
             const int64_t qq = (c + h + 1) >> level;
-            const double* wr = w + (c + h) * N;
+            TV wr[N];
+#pragma unroll
+            for (int p = 0; p < N; ++p) wr[p] = w[(c + h) * N + p];
 #pragma unroll
             for (int i = 0; i < N; ++i)
 #pragma unroll
-                for (int p = 0; p < N; ++p) r[i] = fma(-(double)*RP.at(qq, D::ORL + p * N + i), wr[p], r[i]);
+                for (int p = 0; p < N; ++p) r[i] = fma(-(TV)*RP.at(qq, D::ORL + p * N + i), wr[p], r[i]);
         }
     }
     if (ctz64(c + 1) == level) {
@@ -797,10 +936,10 @@ __device__ void rt_solve_col(int64_t k, int level, int64_t jj, const TR* R, doub
         const int64_t q = (c + 1) >> (level + 1);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            double s = r[i];
+            TV s = r[i];
 #pragma unroll
-            for (int p = 0; p < i; ++p) s = fma(-(double)*RV.at(q, D::ORD + tri(N, p, i)), r[p], s);
-            r[i] = s / (double)*RV.at(q, D::ORD + tri(N, i, i));
+            for (int p = 0; p < i; ++p) s = fma(-(TV)*RV.at(q, D::ORD + tri(N, p, i)), r[p], s);
+            r[i] = s / (TV)*RV.at(q, D::ORD + tri(N, i, i));
         }
 #pragma unroll
         for (int i = 0; i < N; ++i) w[c * N + i] = r[i];
@@ -808,6 +947,46 @@ __device__ void rt_solve_col(int64_t k, int level, int64_t jj, const TR* R, doub
 #pragma unroll
         for (int i = 0; i < N; ++i) g[c * N + i] = r[i];
     }
+}
+
+// R d = w for one row, all in FP32 (the correction of the refinement).
+template <int N>
+__device__ void backsub_row_f(int64_t k, int level, int64_t q, const float* R, const float* w,
+                              float* d) {
+    using D = Dims<N>;
+    const RowView<const float> RV(R, k, level, D::RS);
+    const int64_t c = ((2 * q + 1) << level) - 1;
+    const int64_t a = c - (1LL << level), b = c + (1LL << level);
+    float r[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) r[i] = w[c * N + i];
+    if (a >= 0) {
+        float ua[N];
+#pragma unroll
+        for (int p = 0; p < N; ++p) ua[p] = d[a * N + p];
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int p = 0; p < N; ++p) r[i] = fmaf(-*RV.at(q, D::ORL + i * N + p), ua[p], r[i]);
+    }
+    if (b < k) {
+        float ub[N];
+#pragma unroll
+        for (int p = 0; p < N; ++p) ub[p] = d[b * N + p];
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int p = 0; p < N; ++p) r[i] = fmaf(-*RV.at(q, D::ORR + i * N + p), ub[p], r[i]);
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        float s = r[i];
+#pragma unroll
+        for (int p = i + 1; p < N; ++p) s = fmaf(-*RV.at(q, D::ORD + tri(N, i, p)), r[p], s);
+        r[i] = s / *RV.at(q, D::ORD + tri(N, i, i));
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[c * N + i] = r[i];
 }
 
 }  // namespace small

@@ -2,6 +2,8 @@
 // this file once per N = 1..8 with -DKS_SMALL_N=N).  Each kernel maps one thread to one unit:
 // a step (whitening), a column pair / tail triple (level), a block row (back substitution,
 // SelInv), an alive column (R^T w = g).
+#include <cstdlib>
+
 #include "ks_small.cuh"
 
 #ifndef KS_SMALL_N
@@ -87,11 +89,41 @@ __global__ void __launch_bounds__(BLK) cross_k(int64_t k, const T* Sx, double* c
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(BLK) rt_solve_k(int64_t k, int level, const T* R, double* g,
-                                                  double* w) {
+__global__ void __launch_bounds__(BLK) refine_q_k(RefineArgs a, float* q) {
+    const int64_t i = blockIdx.x * (int64_t)BLK + threadIdx.x;
+    if (i + 1 < a.k) refine_q_step<NN>(a, i, q);
+}
+
+__global__ void __launch_bounds__(BLK) refine_g_k(RefineArgs a, const float* q, float* g) {
+    const int64_t c = blockIdx.x * (int64_t)BLK + threadIdx.x;
+    if (c < a.k) refine_g_col<NN>(a, c, q, g);
+}
+
+__global__ void __launch_bounds__(BLK) rt_solve_k(int64_t k, int level, const float* R, float* g,
+                                                  float* w) {
     const int64_t j = blockIdx.x * (int64_t)BLK + threadIdx.x;
-    if (j < (k >> level)) rt_solve_col<T, NN>(k, level, j, R, g, w);
+    if (j < (k >> level)) rt_solve_col<float, float, NN>(k, level, j, R, g, w);
+}
+
+__global__ void __launch_bounds__(BLK) backsub_f_k(int64_t k, int level, const float* R,
+                                                   const float* w, float* d) {
+    const int64_t q = blockIdx.x * (int64_t)BLK + threadIdx.x;
+    if (q < (k >> level) - (k >> (level + 1))) backsub_row_f<NN>(k, level, q, R, w, d);
+}
+
+__global__ void __launch_bounds__(256) add_k(double* u, const float* d, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)256 + threadIdx.x; i < count; i += (int64_t)gridDim.x * 256)
+        u[i] += (double)d[i];
+}
+
+// Below this many units per launch the level / SelInv launches use one thread block per unit
+// (column-owner kernels, all lanes of a warp share a unit) instead of one thread per unit: a
+// lone lane pays the full cost of every warp instruction, which dominates when a level has too
+// few units to fill the GPU.  KS_TAIL_UNITS overrides the default.
+int64_t tail_units(bool fp32) {
+    const char* v = getenv("KS_TAIL_UNITS");
+    if (v && *v) return atoll(v);
+    return fp32 ? 1024 : 4096;
 }
 
 unsigned grid(int64_t work) {
@@ -113,6 +145,8 @@ cudaError_t level(int64_t nc, int lvl, int64_t k, const void* in, void* out, voi
                   cudaStream_t st) {
     const int64_t nt = nc >> 1;
     if (nt <= 0) return cudaSuccess;
+    if (nt < tail_units(fp32))
+        return launch_level_soa(NN, nc, lvl, k, in, out, R, resid, cn2, cd2, bad, fp32, st);
     const int stash = TileSlots<NN>::COUNT;
     if (fp32) {
         const int smem = stash * BLK * (int)sizeof(float);
@@ -153,6 +187,7 @@ cudaError_t backsub(int64_t k, int lvl, const void* R, const double* w, double* 
 cudaError_t selinv(int64_t k, int lvl, const void* R, void* Sx, double* Sd, unsigned long long* bad,
                    bool fp32, cudaStream_t st) {
     const int64_t rows = (k >> lvl) - (k >> (lvl + 1));
+    if (rows < tail_units(fp32)) return launch_selinv_soa(NN, k, lvl, R, Sx, Sd, bad, fp32, st);
     const int stash = SelinvSlots<NN>::COUNT;
     if (fp32) {
         const int smem = stash * BLK * (int)sizeof(float);
@@ -177,13 +212,27 @@ cudaError_t cross(int64_t k, const void* Sx, double* out, bool fp32, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t rt_solve(int64_t k, int lvl, const void* R, double* g, double* w, bool fp32,
-                     cudaStream_t st) {
-    const int64_t cols = k >> lvl;
-    if (fp32)
-        rt_solve_k<float><<<grid(cols), BLK, 0, st>>>(k, lvl, (const float*)R, g, w);
-    else
-        rt_solve_k<double><<<grid(cols), BLK, 0, st>>>(k, lvl, (const double*)R, g, w);
+cudaError_t refine(const RefineArgs& a, float* q, float* g, float* w, float* d, const void* R,
+                   int L, cudaStream_t st) {
+    const int64_t k = a.k;
+    const float* Rf = static_cast<const float*>(R);
+    if (k > 1) {
+        refine_q_k<<<grid(k - 1), BLK, 0, st>>>(a, q);
+        ++t_launches;
+    }
+    refine_g_k<<<grid(k), BLK, 0, st>>>(a, q, g);
+    ++t_launches;
+    for (int l = 0; l <= L; ++l) {
+        rt_solve_k<<<grid(k >> l), BLK, 0, st>>>(k, l, Rf, g, w);
+        ++t_launches;
+    }
+    for (int l = L; l >= 0; --l) {
+        backsub_f_k<<<grid((k >> l) - (k >> (l + 1))), BLK, 0, st>>>(k, l, Rf, w, d);
+        ++t_launches;
+    }
+    const int64_t cnt = k * NN;
+    int64_t b = (cnt + 255) / 256;
+    add_k<<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, st>>>(const_cast<double*>(a.u), d, cnt);
     ++t_launches;
     return cudaGetLastError();
 }
@@ -194,6 +243,6 @@ cudaError_t rt_solve(int64_t k, int lvl, const void* R, double* g, double* w, bo
 extern const SmallOps KS_CAT(small_ops_, KS_SMALL_N);
 const SmallOps KS_CAT(small_ops_, KS_SMALL_N) = {
     KS_SMALL_N, small::whiten, small::level, small::base, small::backsub,
-    small::selinv, small::cross, small::rt_solve};
+    small::selinv, small::cross, small::refine};
 
 }  // namespace ks

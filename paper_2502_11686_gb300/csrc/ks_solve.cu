@@ -54,7 +54,45 @@ __global__ void backsub_kernel(int n, int64_t k, int level, const TR* __restrict
     for (int i = 0; i < n; ++i) u[c * n + i] = r[i];
 }
 
+// R and SelInv-store access of the column-owner SelInv kernel: AoS rows by original index, or
+// the small-state path's per-level element-major rows.  part 0/1/2 = Rd/Rl/Rr; S part 0/1 = Sl/Sr.
 template <typename T>
+struct SelAos {
+    int n;
+    int64_t k;
+    __device__ SelAos(int n_, int64_t k_) : n(n_), k(k_) {}
+    __device__ T R(const T* Rs, int, int64_t, int64_t c, int part, int r, int cc) const {
+        return Rs[c * rstore_rs(n) + part * n * n + r * n + cc];
+    }
+    __device__ T S(const T* Sx, int, int64_t, int64_t c, int part, int r, int cc) const {
+        return Sx[c * 2 * n * n + part * n * n + r * n + cc];
+    }
+    __device__ void setS(T* Sx, int, int64_t, int64_t c, int part, int r, int cc, T v) const {
+        Sx[c * 2 * n * n + part * n * n + r * n + cc] = v;
+    }
+};
+
+template <typename T>
+struct SelSoa {
+    int n, nt;
+    int64_t k;
+    __device__ SelSoa(int n_, int64_t k_) : n(n_), nt(n_ * (n_ + 1) / 2), k(k_) {}
+    __device__ int64_t rows(int l) const { return (k >> l) - (k >> (l + 1)); }
+    __device__ T R(const T* Rs, int l, int64_t q, int64_t, int part, int r, int cc) const {
+        const int64_t RS = nt + 2 * n * n + n;
+        const int64_t base = (k - (k >> l)) * RS;
+        if (part == 0) return cc >= r ? Rs[base + (int64_t)(r * n - r * (r - 1) / 2 + cc - r) * rows(l) + q] : T(0);
+        return Rs[base + (int64_t)(nt + (part - 1) * n * n + r * n + cc) * rows(l) + q];
+    }
+    __device__ T S(const T* Sx, int l, int64_t q, int64_t, int part, int r, int cc) const {
+        return Sx[(k - (k >> l)) * 2 * n * n + (int64_t)(part * n * n + r * n + cc) * rows(l) + q];
+    }
+    __device__ void setS(T* Sx, int l, int64_t q, int64_t, int part, int r, int cc, T v) const {
+        Sx[(k - (k >> l)) * 2 * n * n + (int64_t)(part * n * n + r * n + cc) * rows(l) + q] = v;
+    }
+};
+
+template <typename T, typename IO>
 __global__ void __launch_bounds__(128) selinv_kernel(int n, int64_t k, int level,
                                                      const T* __restrict__ R, T* __restrict__ Sx,
                                                      double* __restrict__ Sd,
@@ -74,27 +112,22 @@ __global__ void __launch_bounds__(128) selinv_kernel(int n, int64_t k, int level
     if (c >= k) return;
     const int64_t a = c - (1LL << level), b = c + (1LL << level);
     const bool ha = a >= 0, hb = b < k;
-    const T* Rc = R + c * rstore_rs(n);
-    const T* Sab = nullptr;
-    bool sab_t = false;
-    if (ha && hb) {
-        if (ctz64(a + 1) == level + 1) {
-            Sab = Sx + a * 2 * nn + nn;  // Sr_a = S_{a,b}
-        } else {
-            Sab = Sx + b * 2 * nn;       // Sl_b = S_{b,a}
-            sab_t = true;
-        }
-    }
+    const IO io(n, k);
+    // The cross block S_ab: a and b are adjacent one level up, where one of them is eliminated.
+    int sab_src = 0;  // 0 none, 1 Sr_a = S_{a,b}, 2 Sl_b = S_{b,a}
+    if (ha && hb) sab_src = (ctz64(a + 1) == level + 1) ? 1 : 2;
+    const int64_t qa = (a + 1) >> (level + 2), qb = (b + 1) >> (level + 2);
     for (int e = tid; e < nn; e += nth) {
         const int r = e / n, cc = e - r * n;
-        RD[r * L.ldr + cc] = Rc[e];
-        TT[r * L.ldt + cc] = ha ? Rc[nn + e] : T(0);
-        TT[r * L.ldt + n + cc] = hb ? Rc[2 * nn + e] : T(0);
+        RD[r * L.ldr + cc] = io.R(R, level, q, c, 0, r, cc);
+        TT[r * L.ldt + cc] = ha ? io.R(R, level, q, c, 1, r, cc) : T(0);
+        TT[r * L.ldt + n + cc] = hb ? io.R(R, level, q, c, 2, r, cc) : T(0);
         RI[r * L.ldr + cc] = (r == cc) ? T(1) : T(0);
         SII[r * L.lds + cc] = ha ? (T)Sd[a * nn + e] : T(0);
         SII[(n + r) * L.lds + n + cc] = hb ? (T)Sd[b * nn + e] : T(0);
         T x = T(0);
-        if (Sab != nullptr) x = sab_t ? Sab[cc * n + r] : Sab[e];
+        if (sab_src == 1) x = io.S(Sx, level + 1, qa, a, 1, r, cc);
+        else if (sab_src == 2) x = io.S(Sx, level + 1, qb, b, 0, cc, r);
         SII[r * L.lds + n + cc] = x;          // S_ab
         SII[(n + cc) * L.lds + r] = x;        // S_ba = S_ab^T
     }
@@ -127,13 +160,12 @@ __global__ void __launch_bounds__(128) selinv_kernel(int n, int64_t k, int level
         RD[r * L.ldr + cc] = s;
     }
     __syncthreads();
-    T* Sxc = Sx + c * 2 * nn;
     for (int e = tid; e < nn; e += nth) {
         const int r = e / n, cc = e - r * n;
         const T v = T(0.5) * (RD[r * L.ldr + cc] + RD[cc * L.ldr + r]);
         Sd[c * nn + e] = (double)v;
-        Sxc[e] = SL[r * L.ldt + cc];
-        Sxc[nn + e] = SL[r * L.ldt + n + cc];
+        io.setS(Sx, level, q, c, 0, r, cc, SL[r * L.ldt + cc]);
+        io.setS(Sx, level, q, c, 1, r, cc, SL[r * L.ldt + n + cc]);
         if (r == cc && !(v > T(0))) flag_error(bad, ST_SINGULAR, c);
     }
 }
@@ -326,24 +358,35 @@ cudaError_t launch_backsub(int n, int64_t k, int level, const void* R, const dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_selinv(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
-                          unsigned long long* bad, bool fp32, cudaStream_t st) {
+template <template <typename> class IO>
+static cudaError_t launch_selinv_io(int n, int64_t k, int level, const void* R, void* Sx,
+                                    double* Sd, unsigned long long* bad, bool fp32,
+                                    cudaStream_t st) {
     const int64_t cols = ((k >> level) + 1) / 2;
     const SelinvLayout L = selinv_layout(n);
     const int threads = 128;
     const unsigned blocks = (unsigned)cols;
     if (fp32) {
         const size_t smem = sizeof(float) * (size_t)L.total;
-        cudaFuncSetAttribute(selinv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        selinv_kernel<float><<<blocks, threads, smem, st>>>(n, k, level, (const float*)R, (float*)Sx, Sd, bad);
-        ++t_launches;
+        cudaFuncSetAttribute(selinv_kernel<float, IO<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        selinv_kernel<float, IO<float>><<<blocks, threads, smem, st>>>(n, k, level, (const float*)R, (float*)Sx, Sd, bad);
     } else {
         const size_t smem = sizeof(double) * (size_t)L.total;
-        cudaFuncSetAttribute(selinv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        selinv_kernel<double><<<blocks, threads, smem, st>>>(n, k, level, (const double*)R, (double*)Sx, Sd, bad);
-        ++t_launches;
+        cudaFuncSetAttribute(selinv_kernel<double, IO<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        selinv_kernel<double, IO<double>><<<blocks, threads, smem, st>>>(n, k, level, (const double*)R, (double*)Sx, Sd, bad);
     }
+    ++t_launches;
     return cudaGetLastError();
+}
+
+cudaError_t launch_selinv(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
+                          unsigned long long* bad, bool fp32, cudaStream_t st) {
+    return launch_selinv_io<SelAos>(n, k, level, R, Sx, Sd, bad, fp32, st);
+}
+
+cudaError_t launch_selinv_soa(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
+                              unsigned long long* bad, bool fp32, cudaStream_t st) {
+    return launch_selinv_io<SelSoa>(n, k, level, R, Sx, Sd, bad, fp32, st);
 }
 
 cudaError_t launch_cross(int n, int64_t k, const void* Sx, double* cross, bool fp32,

@@ -61,8 +61,16 @@ def run(sm, p, cov=True, cross=False, host=False):
 GRID_K = [1, 2, 3, 4, 5, 6, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 129]
 
 
+@pytest.fixture(params=["thread_per_unit", "block_per_unit"])
+def tail_mode(request, monkeypatch):
+    """The small-state path runs a level / SelInv launch with one thread per unit, or (below a
+    size threshold) with one thread block per unit; force each so both kernels are checked."""
+    monkeypatch.setenv("KS_TAIL_UNITS", "0" if request.param == "thread_per_unit" else "1000000000")
+    return request.param
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 8])
-def test_fp64_grid(sm64, n):
+def test_fp64_grid(sm64, n, tail_mode):
     for k in GRID_K:
         p = inputs.random_problem(k, n, n, seed=1000 * n + k, with_c=True)
         ref = oracle.smooth(p, cross=True)
@@ -76,7 +84,7 @@ def test_fp64_grid(sm64, n):
 
 @pytest.mark.parametrize("pattern", ["gaps", "wide", "narrow", "zero_first"])
 @pytest.mark.parametrize("k", [7, 33, 100])
-def test_fp64_ragged_observations(sm64, pattern, k):
+def test_fp64_ragged_observations(sm64, pattern, k, tail_mode):
     n = 4
     rng = np.random.default_rng(k)
     if pattern == "gaps":
@@ -97,7 +105,7 @@ def test_fp64_ragged_observations(sm64, pattern, k):
     assert rel_cov(got["cov"], ref["cov"]) < TOL64
 
 
-def test_fp64_constant_velocity_workload(sm64):
+def test_fp64_constant_velocity_workload(sm64, tail_mode):
     """k = 1000, n = 4, m = 2, the 2-D constant-velocity workload: states and all covariances."""
     p = inputs.cv_problem(k=1000, seed=0)
     ref = oracle.smooth(p, cross=True)
@@ -191,7 +199,7 @@ def test_bad_arguments(sm64):
 # ---------------------------------------------------------------- FP32 + FP64 refinement
 
 @pytest.mark.parametrize("n", [1, 2, 4, 6, 8])
-def test_refine_grid(sm32, n):
+def test_refine_grid(sm32, n, tail_mode):
     for k in GRID_K:
         p = inputs.random_problem(k, n, n, seed=77 * n + k, with_c=True)
         ref = oracle.smooth(p)
