@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) add_k(double* u, const float* d, int64_t 
 int64_t tail_units(bool fp32) {
     const char* v = getenv("KS_TAIL_UNITS");
     if (v && *v) return atoll(v);
-    return fp32 ? 1024 : 4096;
+    return fp32 ? 1024 : 2048;
 }
 
 unsigned grid(int64_t work) {
