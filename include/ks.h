@@ -80,6 +80,9 @@ typedef struct {
     size_t mem_budget;  /* bytes of device work memory the ctx may hold; 0 = no limit */
     int sync;           /* 1 = each call waits for its work and reports device errors */
     int profile;        /* 1 = time every phase with CUDA events on the ctx's stream */
+    const char *tune_cache; /* file where ks_smooth_batch keeps its tuned launch shapes (read at
+                               the first batch, rewritten after tuning); NULL = keep them in the
+                               ctx only */
 } ks_options;
 
 /* Phases reported by ks_profile_read (indices of phase_ms / phase_launches). */
@@ -90,7 +93,8 @@ typedef enum {
     KS_PHASE_REFINE = 3,   /* FP64 residual, R^T w = g, R d = w, u += d */
     KS_PHASE_SELINV = 4,   /* odd-even SelInv (all levels) and the lag-one gather */
     KS_PHASE_COPY = 5,     /* staging of host arrays in and out */
-    KS_NPHASES = 6
+    KS_PHASE_BATCH = 6,    /* ks_smooth_batch: the whole launch sequence (one CUDA graph) */
+    KS_NPHASES = 7
 } ks_phase;
 
 typedef struct {
@@ -101,7 +105,7 @@ typedef struct {
 } ks_profile;
 
 /* Fills *opt with the defaults: device 0, KS_FP64, ctx-owned stream, no budget, sync = 1,
- * profile = 0. */
+ * profile = 0, tune_cache = NULL. */
 void ks_default_options(ks_options *opt);
 
 /* Creates a context.  opt may be NULL (defaults).  Returns KS_OK, KS_ERR_ARG or KS_ERR_CUDA. */
@@ -121,6 +125,32 @@ ks_status ks_smooth(ks_ctx *ctx, int64_t k, int n, const int32_t *m,
                     const double *F, const double *H, const double *c, const double *K,
                     const double *G, const double *o, const double *C,
                     double *u_out, ks_handle *keep, int64_t *info);
+
+/* One problem of a batch: the arguments of ks_smooth plus its outputs. */
+typedef struct {
+    int64_t k;
+    int n;
+    const int32_t *m;                     /* host [k] */
+    const double *F, *H, *c, *K, *G, *o, *C;
+    double *u_out;                        /* [k][n] */
+    double *cov_out;                      /* [k][n][n], or NULL for states only */
+} ks_problem;
+
+/*
+ * Smooths nprob independent problems of any lengths and state sizes together (the batched form;
+ * the paper treats one problem at a time).  Problems are grouped by state dimension; for every
+ * group each recursion level of the odd-even factorization is ONE launch over the tiles of all
+ * its problems (persistent thread blocks walking a device work list), and likewise for the
+ * whitening, back substitution, refinement and SelInv levels.  The launch sequence is captured
+ * once as a CUDA graph per batch shape (state dimensions, deepest level per group, precision,
+ * covariances or not) and replayed for later batches of that shape, whatever their lengths;
+ * the persistent grid of the heaviest launches is chosen by timing candidates at the first
+ * batch of each group (see ks_options.tune_cache).
+ * status / info: NULL, or [nprob] per-problem status and first failing index.  Returns KS_OK
+ * if every problem succeeded, else the status of the first failing problem.
+ */
+ks_status ks_smooth_batch(ks_ctx *ctx, int nprob, const ks_problem *probs, int *status,
+                          int64_t *info);
 
 /*
  * Covariances of the smoothed states, cov(u_hat_i) = [(R^T R)^{-1}]_{ii}, by the odd-even

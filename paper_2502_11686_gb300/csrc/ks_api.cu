@@ -2,18 +2,7 @@
 // of host arrays, and the launch sequence of one smoothing call:
 //   whitening -> level 0 .. L-1 of the odd-even factorization -> base -> back substitution
 //   (levels L .. 0) [-> FP64 refinement in KS_FP32_REFINE mode] -> copy-out -> status.
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <set>
-#include <string>
-#include <vector>
-
-#include "../../include/ks.h"
-#include "ks_internal.cuh"
+#include "ks_host.h"
 
 using namespace ks;
 
@@ -28,191 +17,7 @@ const SmallOps* small_ops(int n) {
 }
 }  // namespace ks
 
-struct ks_fac {
-    int64_t k = 0;
-    int n = 0;
-    int precision = 0;
-    const SmallOps* small = nullptr;  // small-state path (element-major layouts) or generic
-    void* R = nullptr;        // R store, k records of 3n^2+n elements (T)
-    double* resid = nullptr;  // [2k]: residual parts of the level tiles and of the whitening
-};
-
-struct ks_ctx {
-    int device = 0;
-    int precision = KS_FP64;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    size_t budget = 0;
-    int sync = 1;
-    std::string err;
-    unsigned long long* d_bad = nullptr;
-    unsigned long long* h_bad = nullptr;  // pinned
-    double* h_scalar = nullptr;           // pinned
-    void* ws = nullptr;
-    size_t ws_size = 0;
-    std::set<ks_fac*> facs;
-    int smem_optin = 0;
-    int profile = 0;
-    ks_profile prof{};
-    struct Pending { int phase; cudaEvent_t a, b; };
-    std::vector<Pending> pending;     // recorded phase events not yet read
-    std::vector<cudaEvent_t> spare;   // event pool
-};
-
-namespace {
-
-constexpr int KS_NMAX_API = 64;
-
-ks_status fail(ks_ctx* ctx, ks_status s, const char* fmt, ...) {
-    if (ctx) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        ctx->err = buf;
-    }
-    return s;
-}
-
-#define KS_CUDA(ctx, call)                                                                  \
-    do {                                                                                    \
-        cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess) {                                                            \
-            return fail((ctx), e_ == cudaErrorMemoryAllocation ? KS_ERR_OOM : KS_ERR_CUDA,  \
-                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-        }                                                                                   \
-    } while (0)
-
-bool is_device_ptr(const void* p) {
-    if (p == nullptr) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-// Bump allocator over the ctx workspace (256-byte aligned pieces).
-struct Plan {
-    size_t off = 0;
-    size_t take(size_t bytes) {
-        size_t o = off;
-        off += (bytes + 255) & ~size_t(255);
-        return o;
-    }
-};
-
-ks_status reserve(ks_ctx* ctx, size_t bytes) {
-    if (bytes <= ctx->ws_size) return KS_OK;
-    if (ctx->budget && bytes > ctx->budget)
-        return fail(ctx, KS_ERR_OOM, "work memory %zu bytes exceeds the ctx budget %zu", bytes, ctx->budget);
-    KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (ctx->ws) cudaFree(ctx->ws);
-    ctx->ws = nullptr;
-    ctx->ws_size = 0;
-    KS_CUDA(ctx, cudaMalloc(&ctx->ws, bytes));
-    ctx->ws_size = bytes;
-    return KS_OK;
-}
-
-int tile_smem_bytes(int n, bool fp32) { return tile_layout(n).total * (fp32 ? 4 : 8); }
-int selinv_smem_bytes(int n, bool fp32) { return selinv_layout(n).total * (fp32 ? 4 : 8); }
-int whiten_smem_bytes(int n, int m) { return whiten_layout(n, m).total * 8; }
-
-int max_n_for(const ks_ctx* ctx) {
-    const bool fp32 = ctx->precision == KS_FP32_REFINE;
-    int best = 0;
-    for (int n = 1; n <= KS_NMAX_API; ++n) {
-        if (3 * n + 2 > 256) break;
-        if (tile_smem_bytes(n, fp32) > ctx->smem_optin) break;
-        if (selinv_smem_bytes(n, fp32) > ctx->smem_optin) break;
-        if (whiten_smem_bytes(n, 0) > ctx->smem_optin) break;
-        best = n;
-    }
-    return best;
-}
-
-int max_m_for(const ks_ctx* ctx, int n) {
-    int best = -1;
-    for (int m = 0; m <= KS_NMAX_API; ++m) {
-        if (n + m > 256) break;
-        if (whiten_smem_bytes(n, m) > ctx->smem_optin) break;
-        best = m;
-    }
-    return best;
-}
-
-// Reads the device error words and resets them; returns the most severe code.
-ks_status collect_status(ks_ctx* ctx, int64_t* info) {
-    KS_CUDA(ctx, cudaMemcpyAsync(ctx->h_bad, ctx->d_bad, sizeof(unsigned long long) * ST_NCODES,
-                                 cudaMemcpyDeviceToHost, ctx->stream));
-    KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    KS_CUDA(ctx, cudaMemsetAsync(ctx->d_bad, 0xFF, sizeof(unsigned long long) * ST_NCODES, ctx->stream));
-    static const int order[] = {ST_NOT_SPD, ST_SINGULAR, ST_TIMEOUT, ST_ARG};
-    for (int code : order) {
-        if (ctx->h_bad[code] != ~0ULL) {
-            if (info) *info = (int64_t)ctx->h_bad[code];
-            const char* what = code == ST_NOT_SPD ? "a covariance matrix is not SPD at step"
-                               : code == ST_SINGULAR ? "singular diagonal block of R at state"
-                               : code == ST_TIMEOUT ? "device wait timed out at"
-                                                    : "bad argument detected on device at";
-            return fail(ctx, (ks_status)code, "%s %lld", what, (long long)ctx->h_bad[code]);
-        }
-    }
-    if (info) *info = -1;
-    return KS_OK;
-}
-
-cudaEvent_t get_event(ks_ctx* ctx) {
-    if (!ctx->spare.empty()) {
-        cudaEvent_t e = ctx->spare.back();
-        ctx->spare.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-}
-
-// Brackets the launches of one phase: counts them and, with profiling on, records a pair of
-// events on the ctx's stream around them.
-struct Phase {
-    ks_ctx* ctx;
-    int phase;
-    uint64_t l0;
-    cudaEvent_t a = nullptr;
-    Phase(ks_ctx* c, int ph) : ctx(c), phase(ph), l0(t_launches) {
-        if (ctx->profile) {
-            a = get_event(ctx);
-            cudaEventRecord(a, ctx->stream);
-        }
-    }
-    ~Phase() {
-        const uint64_t nl = t_launches - l0;
-        ctx->prof.launches += nl;
-        ctx->prof.phase_launches[phase] += nl;
-        if (ctx->profile && a) {
-            cudaEvent_t b = get_event(ctx);
-            cudaEventRecord(b, ctx->stream);
-            ctx->pending.push_back({phase, a, b});
-        }
-    }
-};
-
-void drain_profile(ks_ctx* ctx) {
-    for (auto& p : ctx->pending) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) ctx->prof.phase_ms[p.phase] += ms;
-        cudaGetLastError();
-        ctx->spare.push_back(p.a);
-        ctx->spare.push_back(p.b);
-    }
-    ctx->pending.clear();
-}
-
-}  // namespace
+using namespace kshost;
 
 extern "C" {
 
@@ -224,6 +29,7 @@ void ks_default_options(ks_options* opt) {
     opt->mem_budget = 0;
     opt->sync = 1;
     opt->profile = 0;
+    opt->tune_cache = nullptr;
 }
 
 ks_status ks_create(ks_ctx** out, const ks_options* opt) {
@@ -244,6 +50,7 @@ ks_status ks_create(ks_ctx** out, const ks_options* opt) {
     ctx->budget = o.mem_budget;
     ctx->sync = o.sync;
     ctx->profile = o.profile;
+    if (o.tune_cache) ctx->tune_cache = o.tune_cache;
     if (cudaSetDevice(o.device) != cudaSuccess) { delete ctx; return KS_ERR_CUDA; }
     if (o.stream) {
         ctx->stream = (cudaStream_t)o.stream;
@@ -609,6 +416,9 @@ ks_status ks_destroy(ks_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drain_profile(ctx);
     for (cudaEvent_t e : ctx->spare) cudaEventDestroy(e);
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
+    ctx->graphs.clear();
+    if (ctx->bmeta) cudaFree(ctx->bmeta);
     for (ks_fac* f : ctx->facs) {
         cudaFree(f->R);
         cudaFree(f->resid);

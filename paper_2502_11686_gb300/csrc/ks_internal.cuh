@@ -265,6 +265,72 @@ cudaError_t launch_rt_solve(int n, int64_t k, int level, const void* R, double* 
                             bool fp32, cudaStream_t st);
 cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t st);
 
+// ---------------------------------------------------------------------------------------------
+// Batched problems.  Every problem of a batch has a descriptor in device memory; a launch
+// covers the units (steps, tiles, rows ...) of all problems of one class (same n and path) at
+// one level, and maps a global unit index to (problem, local unit) through a prefix sum.  The
+// descriptors and work lists live at fixed device addresses, so a captured CUDA graph of the
+// launch sequence can be replayed for any batch of the same shape.
+struct ProbDesc {
+    int64_t k;
+    int n, m_uniform, mmax, L;
+    const int32_t* m;
+    const int64_t *goff, *coff;
+    const double *F, *H, *c, *K, *G, *o, *C;
+    void* lvl[2];                 // ping-pong level buffers
+    void* R;                      // R store
+    double* resid;                // [2k]
+    double *cn2, *cd2;            // [k][n] each
+    double* u;                    // smoothed states [k][n]
+    double *LK, *LC;              // Cholesky factors (refine mode)
+    void *q, *g, *w, *d;          // refinement vectors
+    void* Sx;                     // SelInv store
+    double* cov;                  // covariances [k][n][n] or nullptr
+    unsigned long long* bad;      // this problem's error words [ST_NCODES]
+};
+
+struct BatchWork {
+    const ProbDesc* desc;  // all problems of the batch
+    const int* probs;      // the problems of this launch's class
+    const int64_t* off;    // prefix sum of units per problem [np + 1]
+    int np;
+    int level;
+};
+
+// Index into probs of the problem owning global unit u (off[p] <= u < off[p+1]).
+__device__ __forceinline__ int batch_find(const int64_t* off, int np, int64_t u) {
+    int lo = 0, hi = np;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ WhitenArgs whiten_args_of(const ProbDesc& P) {
+    WhitenArgs a;
+    a.k = P.k; a.n = P.n; a.mmax = P.mmax; a.m_uniform = P.m_uniform;
+    a.m = P.m; a.goff = P.goff; a.coff = P.coff;
+    a.F = P.F; a.H = P.H; a.c = P.c; a.K = P.K; a.G = P.G; a.o = P.o; a.C = P.C;
+    a.level0 = P.lvl[0]; a.resid = P.resid + P.k; a.LK = P.LK; a.LC = P.LC;
+    a.cn2 = P.cn2; a.cd2 = P.cd2; a.bad = P.bad;
+    return a;
+}
+
+__device__ __forceinline__ RefineArgs refine_args_of(const ProbDesc& P) {
+    RefineArgs a;
+    a.k = P.k; a.n = P.n; a.m_uniform = P.m_uniform; a.m = P.m; a.goff = P.goff; a.coff = P.coff;
+    a.F = P.F; a.H = P.H; a.c = P.c; a.G = P.G; a.o = P.o; a.LK = P.LK; a.LC = P.LC;
+    a.u = P.u; a.g = (double*)P.g; a.q = (double*)P.q;
+    return a;
+}
+
+// Batched launches of one class: `grid` blocks, persistent over the work list.
+enum BatchOp {
+    B_WHITEN = 0, B_LEVEL, B_BASE, B_BACKSUB, B_SELINV, B_REFINE_Q, B_REFINE_G, B_RT_SOLVE,
+    B_BACKSUB_W, B_ADD, B_NOPS
+};
+
 // Kernels of the small-state path (one thread per step / tile / row, element-major layouts),
 // one table per compile-time N.  small_ops(n) is nullptr when n has no table.
 struct SmallOps {
@@ -283,7 +349,13 @@ struct SmallOps {
     // Refinement (FP32 mode only): q, g from FP64 residuals; R^T w = g; R d = w; u += d.
     cudaError_t (*refine)(const RefineArgs& a, float* q, float* g, float* w, float* d,
                           const void* R, int L, cudaStream_t);
+    // Batched form: one launch of operation `op` over the work list at `wk` (device memory).
+    cudaError_t (*batch)(int op, const BatchWork* wk, bool fp32, unsigned grid, cudaStream_t);
 };
+
+// Batched column-owner launches (classes with n > 8 or some m_i > n).
+cudaError_t launch_batch_generic(int op, int n, int mmax, const BatchWork* wk, bool fp32,
+                                 unsigned grid, cudaStream_t st);
 const SmallOps* small_ops(int n);
 constexpr int SMALL_NMAX = 8;
 

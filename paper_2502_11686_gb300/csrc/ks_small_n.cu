@@ -126,6 +126,104 @@ int64_t tail_units(bool fp32) {
     return fp32 ? 1024 : 2048;
 }
 
+// ---- batched form: one launch covers one operation for every problem of a class ----------
+template <typename T>
+__device__ void base_one(int64_t k, int L, const T* in, T* R, const double* cn2,
+                         const double* cd2, unsigned long long* bad) {
+    using D = Dims<NN>;
+    const LevelView<const T, NN> I(in, 1);
+    const RowView<T> RV(R, k, L, D::RS);
+    const int64_t c = (1LL << L) - 1;
+    T Tm[NN][NN];
+    load_upper<T, NN>(I, 0, Tm);
+    check_diag<T, NN>(Tm, cn2, cd2, c, bad);
+    for (int r = 0; r < NN; ++r) {
+        for (int cc = r; cc < NN; ++cc) *RV.at(0, D::ORD + tri(NN, r, cc)) = Tm[r][cc];
+        for (int cc = 0; cc < NN; ++cc) {
+            *RV.at(0, D::ORL + r * NN + cc) = T(0);
+            *RV.at(0, D::ORR + r * NN + cc) = T(0);
+        }
+        *RV.at(0, D::OY + r) = *I.at(0, D::ORC + r);
+    }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(BLK) batch_k(const BatchWork* wk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Stash<T> st{reinterpret_cast<T*>(smem_raw), BLK, (int)threadIdx.x};
+    const BatchWork w = *wk;
+    const int64_t total = w.off[w.np];
+    const int l = w.level;
+    for (int64_t u = blockIdx.x * (int64_t)BLK + threadIdx.x; u < total;
+         u += (int64_t)gridDim.x * BLK) {
+        const int pi = batch_find(w.off, w.np, u);
+        const ProbDesc& P = w.desc[w.probs[pi]];
+        const int64_t x = u - w.off[pi];
+        if constexpr (OP == B_WHITEN) {
+            whiten_step<T, NN>(whiten_args_of(P), x, reinterpret_cast<T*>(P.lvl[0]));
+        } else if constexpr (OP == B_LEVEL) {
+            level_tile<T, NN>(P.k >> l, l, P.k, x, reinterpret_cast<const T*>(P.lvl[l & 1]),
+                              reinterpret_cast<T*>(P.lvl[(l + 1) & 1]), reinterpret_cast<T*>(P.R),
+                              P.resid, P.cn2, P.cd2, P.bad, st);
+        } else if constexpr (OP == B_BASE) {
+            base_one<T>(P.k, P.L, reinterpret_cast<const T*>(P.lvl[P.L & 1]),
+                        reinterpret_cast<T*>(P.R), P.cn2, P.cd2, P.bad);
+        } else if constexpr (OP == B_BACKSUB) {
+            backsub_row<T, NN>(P.k, l, x, reinterpret_cast<const T*>(P.R), nullptr, P.u);
+        } else if constexpr (OP == B_SELINV) {
+            selinv_row<T, NN>(P.k, l, x, reinterpret_cast<const T*>(P.R), reinterpret_cast<T*>(P.Sx),
+                              P.cov, P.bad, st);
+        } else if constexpr (OP == B_REFINE_Q) {
+            refine_q_step<NN>(refine_args_of(P), x, reinterpret_cast<float*>(P.q));
+        } else if constexpr (OP == B_REFINE_G) {
+            refine_g_col<NN>(refine_args_of(P), x, reinterpret_cast<const float*>(P.q),
+                             reinterpret_cast<float*>(P.g));
+        } else if constexpr (OP == B_RT_SOLVE) {
+            rt_solve_col<float, float, NN>(P.k, l, x, reinterpret_cast<const float*>(P.R),
+                                           reinterpret_cast<float*>(P.g), reinterpret_cast<float*>(P.w));
+        } else if constexpr (OP == B_BACKSUB_W) {
+            backsub_row_f<NN>(P.k, l, x, reinterpret_cast<const float*>(P.R),
+                              reinterpret_cast<const float*>(P.w), reinterpret_cast<float*>(P.d));
+        } else if constexpr (OP == B_ADD) {
+            P.u[x] += (double)reinterpret_cast<const float*>(P.d)[x];
+        }
+    }
+}
+
+template <typename T, int OP>
+cudaError_t batch_launch(const BatchWork* wk, unsigned grid, int smem, cudaStream_t st) {
+    if (smem > 0) cudaFuncSetAttribute(batch_k<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    batch_k<T, OP><<<grid, BLK, smem, st>>>(wk);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t batch_t(int op, const BatchWork* wk, unsigned grid, cudaStream_t st) {
+    const int lvl_smem = TileSlots<NN>::COUNT * BLK * (int)sizeof(T);
+    const int sel_smem = SelinvSlots<NN>::COUNT * BLK * (int)sizeof(T);
+    switch (op) {
+        case B_WHITEN: return batch_launch<T, B_WHITEN>(wk, grid, 0, st);
+        case B_LEVEL: return batch_launch<T, B_LEVEL>(wk, grid, lvl_smem, st);
+        case B_BASE: return batch_launch<T, B_BASE>(wk, grid, 0, st);
+        case B_BACKSUB: return batch_launch<T, B_BACKSUB>(wk, grid, 0, st);
+        case B_SELINV: return batch_launch<T, B_SELINV>(wk, grid, sel_smem, st);
+        case B_REFINE_Q: return batch_launch<T, B_REFINE_Q>(wk, grid, 0, st);
+        case B_REFINE_G: return batch_launch<T, B_REFINE_G>(wk, grid, 0, st);
+        case B_RT_SOLVE: return batch_launch<T, B_RT_SOLVE>(wk, grid, 0, st);
+        case B_BACKSUB_W: return batch_launch<T, B_BACKSUB_W>(wk, grid, 0, st);
+        case B_ADD: return batch_launch<T, B_ADD>(wk, grid, 0, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t batch(int op, const BatchWork* wk, bool fp32, unsigned grid, cudaStream_t st) {
+    if (fp32) return batch_t<float>(op, wk, grid, st);
+    // FP64 mode has no refinement operations.
+    if (op >= B_REFINE_Q) return cudaErrorInvalidValue;
+    return batch_t<double>(op, wk, grid, st);
+}
+
 unsigned grid(int64_t work) {
     int64_t b = (work + BLK - 1) / BLK;
     return (unsigned)(b < 1 ? 1 : b);
@@ -243,6 +341,6 @@ cudaError_t refine(const RefineArgs& a, float* q, float* g, float* w, float* d, 
 extern const SmallOps KS_CAT(small_ops_, KS_SMALL_N);
 const SmallOps KS_CAT(small_ops_, KS_SMALL_N) = {
     KS_SMALL_N, small::whiten, small::level, small::base, small::backsub,
-    small::selinv, small::cross, small::refine};
+    small::selinv, small::cross, small::refine, small::batch};
 
 }  // namespace ks

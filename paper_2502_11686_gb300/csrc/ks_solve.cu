@@ -11,7 +11,9 @@
 //    the corrected semi-normal equations R^T R d = g with the FP32 R: R^T w = g level by level
 //    from the bottom (column c pulls the blocks of the rows eliminated below it that touch it),
 //    then R d = w by back substitution, u += d.
-#include "ks_internal.cuh"
+#include <algorithm>
+
+#include "ks_generic.cuh"
 
 namespace ks {
 
@@ -20,9 +22,8 @@ constexpr int KS_NMAX = 64;
 __device__ __forceinline__ int ctz64(int64_t x) { return __ffsll((long long)x) - 1; }
 
 template <typename TR>
-__global__ void backsub_kernel(int n, int64_t k, int level, const TR* __restrict__ R,
-                               const double* __restrict__ w, double* __restrict__ u) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ void backsub_row_generic(int n, int64_t k, int level, int64_t q, const TR* __restrict__ R,
+                                    const double* __restrict__ w, double* __restrict__ u) {
     const int64_t c = ((2 * q + 1) << level) - 1;
     if (c >= k) return;
     const int nn = n * n;
@@ -52,6 +53,12 @@ __global__ void backsub_kernel(int n, int64_t k, int level, const TR* __restrict
         r[i] = s / (double)Rc[i * n + i];
     }
     for (int i = 0; i < n; ++i) u[c * n + i] = r[i];
+}
+
+template <typename TR>
+__global__ void backsub_kernel(int n, int64_t k, int level, const TR* __restrict__ R,
+                               const double* __restrict__ w, double* __restrict__ u) {
+    backsub_row_generic<TR>(n, k, level, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, R, w, u);
 }
 
 // R and SelInv-store access of the column-owner SelInv kernel: AoS rows by original index, or
@@ -92,13 +99,12 @@ struct SelSoa {
     }
 };
 
+// Row q of level `level` (Algorithm 2 body), column-owner scheme: every thread of the block
+// must call it.
 template <typename T, typename IO>
-__global__ void __launch_bounds__(128) selinv_kernel(int n, int64_t k, int level,
-                                                     const T* __restrict__ R, T* __restrict__ Sx,
-                                                     double* __restrict__ Sd,
-                                                     unsigned long long* bad) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sm = reinterpret_cast<T*>(smem_raw);
+__device__ void selinv_cta_row(int n, int64_t k, int level, int64_t q, const T* __restrict__ R,
+                               T* __restrict__ Sx, double* __restrict__ Sd,
+                               unsigned long long* bad, T* sm) {
     const SelinvLayout L = selinv_layout(n);
     T* RD = sm + L.rd;
     T* TT = sm + L.tt;
@@ -107,7 +113,6 @@ __global__ void __launch_bounds__(128) selinv_kernel(int n, int64_t k, int level
     T* SL = sm + L.sl;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int nn = n * n;
-    const int64_t q = blockIdx.x;
     const int64_t c = ((2 * q + 1) << level) - 1;
     if (c >= k) return;
     const int64_t a = c - (1LL << level), b = c + (1LL << level);
@@ -168,6 +173,16 @@ __global__ void __launch_bounds__(128) selinv_kernel(int n, int64_t k, int level
         io.setS(Sx, level, q, c, 1, r, cc, SL[r * L.ldt + n + cc]);
         if (r == cc && !(v > T(0))) flag_error(bad, ST_SINGULAR, c);
     }
+    __syncthreads();
+}
+
+template <typename T, typename IO>
+__global__ void __launch_bounds__(128) selinv_kernel(int n, int64_t k, int level,
+                                                     const T* __restrict__ R, T* __restrict__ Sx,
+                                                     double* __restrict__ Sd,
+                                                     unsigned long long* bad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    selinv_cta_row<T, IO>(n, k, level, blockIdx.x, R, Sx, Sd, bad, reinterpret_cast<T*>(smem_raw));
 }
 
 template <typename T>
@@ -201,8 +216,7 @@ __global__ void sum_kernel(const double* __restrict__ x, int64_t count, double* 
 }
 
 // q_i = K_i^{-1} (F_i u_i + c_i - H_i u_{i+1}) with K_i = L_K L_K^T (one thread per step).
-__global__ void refine_q_kernel(RefineArgs a) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ void refine_q_generic(const RefineArgs& a, int64_t i) {
     if (i + 1 >= a.k) return;
     const int n = a.n, nn = n * n;
     const double* F = a.F + i * nn;
@@ -230,9 +244,12 @@ __global__ void refine_q_kernel(RefineArgs a) {
     for (int r = 0; r < n; ++r) a.q[i * n + r] = e[r];
 }
 
+__global__ void refine_q_kernel(RefineArgs a) {
+    refine_q_generic(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+
 // g_c = H_{c-1}^T q_{c-1} - F_c^T q_c + G_c^T C_c^{-1} (o_c - G_c u_c).
-__global__ void refine_g_kernel(RefineArgs a) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ void refine_g_generic(const RefineArgs& a, int64_t c) {
     if (c >= a.k) return;
     const int n = a.n, nn = n * n;
     double g[KS_NMAX];
@@ -286,13 +303,16 @@ __global__ void refine_g_kernel(RefineArgs a) {
     for (int r = 0; r < n; ++r) a.g[c * n + r] = g[r];
 }
 
+__global__ void refine_g_kernel(RefineArgs a) {
+    refine_g_generic(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+
 // R^T w = g at one level: every column alive at `level` first pulls the blocks of the rows
 // eliminated at level-1 that touch it (rows c -+ 2^{level-1}), then, if it is eliminated at
 // `level`, solves Rd_c^T w_c = g_c.
 template <typename TR>
-__global__ void rt_solve_kernel(int n, int64_t k, int level, const TR* __restrict__ R,
-                                double* __restrict__ g, double* __restrict__ w) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ void rt_solve_generic(int n, int64_t k, int level, int64_t j, const TR* __restrict__ R,
+                                 double* __restrict__ g, double* __restrict__ w) {
     if (j >= (k >> level)) return;
     const int64_t c = ((j + 1) << level) - 1;
     const int nn = n * n;
@@ -331,6 +351,12 @@ __global__ void rt_solve_kernel(int n, int64_t k, int level, const TR* __restric
     } else {
         for (int i = 0; i < n; ++i) g[c * n + i] = r[i];
     }
+}
+
+template <typename TR>
+__global__ void rt_solve_kernel(int n, int64_t k, int level, const TR* __restrict__ R,
+                                double* __restrict__ g, double* __restrict__ w) {
+    rt_solve_generic<TR>(n, k, level, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, R, g, w);
 }
 
 __global__ void axpy_kernel(double* __restrict__ u, const double* __restrict__ d, int64_t count) {
@@ -434,6 +460,95 @@ cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t 
     axpy_kernel<<<grid_for(count, 256) > 4096 ? 4096 : grid_for(count, 256), 256, 0, st>>>(u, d, count);
     ++t_launches;
     return cudaGetLastError();
+}
+
+// ---- batched column-owner launches ----------------------------------------------------------
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) batch_generic_k(const BatchWork* wk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const BatchWork w = *wk;
+    const int64_t total = w.off[w.np];
+    const int l = w.level;
+    constexpr bool per_block = (OP == B_WHITEN || OP == B_LEVEL || OP == B_BASE || OP == B_SELINV);
+    const int64_t first = per_block ? blockIdx.x : blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = per_block ? gridDim.x : (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = first; u < total; u += stride) {
+        const int pi = batch_find(w.off, w.np, u);
+        const ProbDesc& P = w.desc[w.probs[pi]];
+        const int64_t x = u - w.off[pi];
+        const int n = P.n;
+        if constexpr (OP == B_WHITEN) {
+            whiten_cta_step<T>(whiten_args_of(P), x, reinterpret_cast<double*>(smem_raw));
+        } else if constexpr (OP == B_LEVEL) {
+            const int64_t nc = P.k >> l;
+            const AosIO<T> io(n, nc, l, P.k, reinterpret_cast<const T*>(P.lvl[l & 1]),
+                              reinterpret_cast<T*>(P.lvl[(l + 1) & 1]), reinterpret_cast<T*>(P.R));
+            level_cta_tile<T, AosIO<T>>(io, n, nc, l, x, P.resid, P.cn2, P.cd2, P.bad,
+                                        reinterpret_cast<T*>(smem_raw));
+        } else if constexpr (OP == B_BASE) {
+            base_block<T>(n, P.k, P.L, reinterpret_cast<const T*>(P.lvl[P.L & 1]),
+                          reinterpret_cast<T*>(P.R), P.cn2, P.cd2, P.bad);
+            __syncthreads();
+        } else if constexpr (OP == B_BACKSUB) {
+            backsub_row_generic<T>(n, P.k, l, x, reinterpret_cast<const T*>(P.R), nullptr, P.u);
+        } else if constexpr (OP == B_SELINV) {
+            selinv_cta_row<T, SelAos<T>>(n, P.k, l, x, reinterpret_cast<const T*>(P.R),
+                                         reinterpret_cast<T*>(P.Sx), P.cov, P.bad,
+                                         reinterpret_cast<T*>(smem_raw));
+        } else if constexpr (OP == B_REFINE_Q) {
+            refine_q_generic(refine_args_of(P), x);
+        } else if constexpr (OP == B_REFINE_G) {
+            refine_g_generic(refine_args_of(P), x);
+        } else if constexpr (OP == B_RT_SOLVE) {
+            rt_solve_generic<T>(n, P.k, l, x, reinterpret_cast<const T*>(P.R),
+                                reinterpret_cast<double*>(P.g), reinterpret_cast<double*>(P.w));
+        } else if constexpr (OP == B_BACKSUB_W) {
+            backsub_row_generic<T>(n, P.k, l, x, reinterpret_cast<const T*>(P.R),
+                                   reinterpret_cast<const double*>(P.w), reinterpret_cast<double*>(P.d));
+        } else if constexpr (OP == B_ADD) {
+            P.u[x] += reinterpret_cast<const double*>(P.d)[x];
+        }
+    }
+}
+
+template <typename T, int OP>
+static cudaError_t batch_generic_launch(const BatchWork* wk, unsigned grid, int threads, size_t smem,
+                                        cudaStream_t st) {
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(batch_generic_k<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    batch_generic_k<T, OP><<<grid, threads, smem, st>>>(wk);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t batch_generic_t(int op, int n, int mmax, const BatchWork* wk, unsigned grid,
+                                   cudaStream_t st) {
+    const int wthreads = ((std::max(3 * n + 2, n + mmax) + 31) / 32) * 32;
+    const int lthreads = ((3 * n + 1 + 31) / 32) * 32;
+    switch (op) {
+        case B_WHITEN:
+            return batch_generic_launch<T, B_WHITEN>(wk, grid, wthreads,
+                                                     sizeof(double) * (size_t)whiten_layout(n, mmax).total, st);
+        case B_LEVEL:
+            return batch_generic_launch<T, B_LEVEL>(wk, grid, lthreads, sizeof(T) * (size_t)tile_layout(n).total, st);
+        case B_BASE: return batch_generic_launch<T, B_BASE>(wk, grid, 128, 0, st);
+        case B_BACKSUB: return batch_generic_launch<T, B_BACKSUB>(wk, grid, 128, 0, st);
+        case B_SELINV:
+            return batch_generic_launch<T, B_SELINV>(wk, grid, 128, sizeof(T) * (size_t)selinv_layout(n).total, st);
+        case B_REFINE_Q: return batch_generic_launch<T, B_REFINE_Q>(wk, grid, 128, 0, st);
+        case B_REFINE_G: return batch_generic_launch<T, B_REFINE_G>(wk, grid, 128, 0, st);
+        case B_RT_SOLVE: return batch_generic_launch<T, B_RT_SOLVE>(wk, grid, 128, 0, st);
+        case B_BACKSUB_W: return batch_generic_launch<T, B_BACKSUB_W>(wk, grid, 128, 0, st);
+        case B_ADD: return batch_generic_launch<T, B_ADD>(wk, grid, 256, 0, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_generic(int op, int n, int mmax, const BatchWork* wk, bool fp32,
+                                 unsigned grid, cudaStream_t st) {
+    return fp32 ? batch_generic_t<float>(op, n, mmax, wk, grid, st)
+                : batch_generic_t<double>(op, n, mmax, wk, grid, st);
 }
 
 }  // namespace ks

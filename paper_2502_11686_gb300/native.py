@@ -22,19 +22,27 @@ KS_FP64, KS_FP32_REFINE = 0, 1
 # Every symbol include/ks.h declares.
 EXPORTS = ("ks_default_options", "ks_create", "ks_smooth", "ks_covariances", "ks_residual",
            "ks_release", "ks_sync", "ks_destroy", "ks_last_error", "ks_max_n", "ks_max_m",
-           "ks_profile_read", "ks_smooth_static")
-PHASES = ("whiten", "level", "backsub", "refine", "selinv", "copy")
+           "ks_profile_read", "ks_smooth_static", "ks_smooth_batch")
+PHASES = ("whiten", "level", "backsub", "refine", "selinv", "copy", "batch")
 
 
 class ks_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("precision", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
-                ("sync", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("sync", ctypes.c_int), ("profile", ctypes.c_int),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class ks_profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64), ("phase_launches", ctypes.c_uint64 * 6),
-                ("phase_ms", ctypes.c_double * 6), ("calls", ctypes.c_uint64)]
+    _fields_ = [("launches", ctypes.c_uint64), ("phase_launches", ctypes.c_uint64 * 7),
+                ("phase_ms", ctypes.c_double * 7), ("calls", ctypes.c_uint64)]
+
+
+class ks_problem(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("n", ctypes.c_int), ("m", ctypes.c_void_p),
+                ("F", ctypes.c_void_p), ("H", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("K", ctypes.c_void_p), ("G", ctypes.c_void_p), ("o", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("u_out", ctypes.c_void_p), ("cov_out", ctypes.c_void_p)]
 
 
 class KsError(RuntimeError):
@@ -88,6 +96,9 @@ def load():
         lib.ks_smooth_static.argtypes = [I, P, I64, I, I, P, P, P, P, P, P, P, P, P,
                                          ctypes.POINTER(I64), ctypes.c_char_p, ctypes.c_size_t]
         lib.ks_smooth_static.restype = I
+        lib.ks_smooth_batch.argtypes = [P, I, ctypes.POINTER(ks_problem), ctypes.POINTER(I),
+                                        ctypes.POINTER(I64)]
+        lib.ks_smooth_batch.restype = I
         _lib = lib
         return lib
 
@@ -183,8 +194,8 @@ def ks_profile_read(ctx, reset=False) -> dict:
     pr = ks_profile()
     _check(ctx, load().ks_profile_read(ctx, ctypes.byref(pr), 1 if reset else 0))
     return {"launches": int(pr.launches), "calls": int(pr.calls),
-            "phase_launches": {PHASES[i]: int(pr.phase_launches[i]) for i in range(6)},
-            "phase_ms": {PHASES[i]: float(pr.phase_ms[i]) for i in range(6)}}
+            "phase_launches": {PHASES[i]: int(pr.phase_launches[i]) for i in range(7)},
+            "phase_ms": {PHASES[i]: float(pr.phase_ms[i]) for i in range(7)}}
 
 
 def ks_smooth_static(device, stream, k, n, m, F, H, c, K, G, o, C, u_out, cov_out=None):
@@ -196,3 +207,24 @@ def ks_smooth_static(device, stream, k, n, m, F, H, c, K, G, o, C, u_out, cov_ou
                                  ptr(c), ptr(K), ptr(G), ptr(o), ptr(C), ptr(u_out),
                                  ptr(cov_out), ctypes.byref(info), buf, len(buf))
     return st, info.value, buf.value.decode()
+
+
+def ks_smooth_batch(ctx, problems, check=True):
+    """problems: list of dicts with k, n, m and the arrays of ks_smooth plus u_out / cov_out.
+    Returns (status, per-problem statuses, per-problem infos)."""
+    arr = (ks_problem * len(problems))()
+    keep = []
+    for i, p in enumerate(problems):
+        m = p["m"]
+        keep.append(m)
+        arr[i] = ks_problem(int(p["k"]), int(p["n"]), ptr(m), ptr(p.get("F")), ptr(p.get("H")),
+                            ptr(p.get("c")), ptr(p.get("K")), ptr(p.get("G")), ptr(p.get("o")),
+                            ptr(p.get("C")), ptr(p["u_out"]), ptr(p.get("cov_out")))
+    st_arr = (ctypes.c_int * len(problems))()
+    info_arr = (ctypes.c_int64 * len(problems))()
+    st = load().ks_smooth_batch(ctx, len(problems), arr, st_arr, info_arr)
+    if check and st != KS_OK:
+        bad = [i for i in range(len(problems)) if st_arr[i] != KS_OK]
+        raise KsError(st, ks_last_error(ctx) + f" (problems {bad[:8]})",
+                      info_arr[bad[0]] if bad else -1)
+    return st, list(st_arr), list(info_arr)
