@@ -48,6 +48,13 @@ WORKLOADS = {
 }
 
 
+BATCH_WORKLOADS = {
+    "batch_c4": dict(nprob=512, k_lo=100, k_hi=20000, ns=(4, 8, 16, 32),
+                     desc="512 independent problems, k log-uniform [100, 20000], n in {4, 8, 16, "
+                          "32}, m = n/2 or n, problem i from seed i; states + all covariances"),
+}
+
+
 def make_problem(wl, seed, k=None):
     from paper_2502_11686_gb300 import inputs
     k = k or wl["k"]
@@ -210,19 +217,150 @@ def reference_arm(args, wl):
     return 0
 
 
+def batch_arm(args):
+    """The batched form: every step is one ks_smooth_batch call over resident inputs."""
+    import torch
+
+    import oracle
+    from paper_2502_11686_gb300 import inputs, native, problem_arrays
+
+    wl = BATCH_WORKLOADS[args.workload]
+    nprob = args.nprob or wl["nprob"]
+    torch.cuda.set_device(0)
+    probs = inputs.uneven_batch(nprob, 0, wl["k_lo"], wl["k_hi"], wl["ns"])
+    total_k = sum(p.k for p in probs)
+    batch = []
+    for p in probs:
+        arr = problem_arrays(p, "cuda:0")
+        d = dict(arr, k=p.k, n=p.n, m=np.ascontiguousarray(p.m, dtype=np.int32),
+                 u_out=torch.empty((p.k, p.n), dtype=torch.float64, device="cuda:0"),
+                 cov_out=torch.empty((p.k, p.n, p.n), dtype=torch.float64, device="cuda:0"))
+        batch.append(d)
+    stream = torch.cuda.Stream()
+    prec = native.KS_FP64 if args.precision == "fp64" else native.KS_FP32_REFINE
+
+    def make_ctx(profile):
+        o = native.ks_default_options()
+        o.precision = prec
+        o.stream = stream.cuda_stream
+        o.profile = 1 if profile else 0
+        return native.ks_create(o)
+
+    ctx = make_ctx(False)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            native.ks_smooth_batch(ctx, batch)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                native.ks_smooth_batch(ctx, batch)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof_graph = native.ks_profile_read(ctx)
+    native.ks_destroy(ctx)
+    value = total_k * args.steps / (ms / 1e3)
+
+    # One profiled pass (launches issued one by one, each timed into its phase).
+    pctx = make_ctx(True)
+    with torch.cuda.stream(stream):
+        native.ks_smooth_batch(pctx, batch)
+        native.ks_profile_read(pctx, reset=True)
+        native.ks_smooth_batch(pctx, batch)
+    prof = native.ks_profile_read(pctx)
+    native.ks_destroy(pctx)
+    phase_ms = {k: v for k, v in prof["phase_ms"].items() if v > 0 and k != "copy"}
+
+    # The same problems one at a time in FP64 (ks_smooth + ks_covariances per problem).
+    o = native.ks_default_options()
+    o.stream = stream.cuda_stream
+    o.sync = 0
+    c64 = native.ks_create(o)
+    def per_problem():
+        for b in batch:
+            _, h, _ = native.ks_smooth(c64, b["k"], b["n"], b["m"], b["F"], b["H"], b["c"], b["K"],
+                                       b["G"], b["o"], b["C"], b["u_out"], keep=True)
+            native.ks_covariances(c64, h, b["cov_out"])
+            native.ks_release(c64, h)
+    with torch.cuda.stream(stream):
+        per_problem()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        per_problem()
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    per_problem_fp64 = total_k / (ev0.elapsed_time(ev1) / 1e3)
+    native.ks_destroy(c64)
+
+    # Roofline of the dominant phase: algorithmic flops summed over the problems.
+    flops = {ph: 0.0 for ph in ("whiten", "level", "backsub", "selinv", "refine")}
+    for p in probs:
+        f = flops_per_step(p.n, int(p.m[0]), args.precision)
+        for ph in flops:
+            flops[ph] += f[ph] * p.k
+    top = max(flops, key=lambda ph: phase_ms.get(ph, 0.0))
+    achieved = flops[top] / (phase_ms[top] / 1e3) / 1e12
+    fp64_phase = args.precision == "fp64" or top in ("whiten", "refine")
+    peak = FP64_PEAK_TFLOPS if fp64_phase else FP32_PEAK_TFLOPS
+    roof = {"bound": "alu", "kernel": f"{top} phase (batched launches)", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": ("nominal FP64 rate of the GB300 (1.25 TFLOP/s)" if fp64_phase else
+                            "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
+            "traffic": None}
+    cpu = None
+    if not args.no_cpu_baseline:
+        t0, steps, i = time.perf_counter(), 0, 0
+        while time.perf_counter() - t0 < 10.0:
+            p = probs[i % len(probs)]
+            oracle.smooth(p)
+            steps += p.k
+            i += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the first {i} problems of the batch, one after another, states + "
+                         f"covariances, {el:.1f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {wl['desc']}", "problems": nprob,
+                   "total_states": total_k, "precision": args.precision,
+                   "l2": "inputs larger than L2, no flush",
+                   "parallelism": "replicas only (independent problems)"},
+        "per_problem_fp64_steps_per_s": per_problem_fp64,
+        "roofline": roof, "phase_ms_per_step": phase_ms, "cpu_baseline": cpu, "e2e": None,
+        "gpu_launches": prof_graph["launches"] // max(1, args.steps + args.warmup) * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="long_k1e6_n6", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="long_k1e6_n6",
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
+    ap.add_argument("--nprob", type=int, default=None, help="batched workloads: problem count")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_refine"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--k", type=int, default=None,
                     help="override the number of states (smaller cases for profiling)")
     args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.workload in BATCH_WORKLOADS:
+        if args.impl == "reference":
+            return 0
+        return batch_arm(args)
     wl = dict(WORKLOADS[args.workload])
     if args.k:
         wl["k"] = args.k

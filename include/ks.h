@@ -126,6 +126,11 @@ ks_status ks_smooth(ks_ctx *ctx, int64_t k, int n, const int32_t *m,
                     const double *G, const double *o, const double *C,
                     double *u_out, ks_handle *keep, int64_t *info);
 
+/* Bits of ks_problem.time_invariant: the array holds ONE matrix used at every step (a
+ * time-invariant model) instead of one per step.  G and C may be time invariant only if every
+ * m_i is the same. */
+enum { KS_TI_F = 1, KS_TI_H = 2, KS_TI_K = 4, KS_TI_G = 8, KS_TI_C = 16 };
+
 /* One problem of a batch: the arguments of ks_smooth plus its outputs. */
 typedef struct {
     int64_t k;
@@ -134,6 +139,7 @@ typedef struct {
     const double *F, *H, *c, *K, *G, *o, *C;
     double *u_out;                        /* [k][n] */
     double *cov_out;                      /* [k][n][n], or NULL for states only */
+    unsigned time_invariant;              /* KS_TI_* bits (0 = every array per step) */
 } ks_problem;
 
 /*
@@ -151,6 +157,73 @@ typedef struct {
  */
 ks_status ks_smooth_batch(ks_ctx *ctx, int nprob, const ks_problem *probs, int *status,
                           int64_t *info);
+
+/*
+ * Synthetic time-invariant problem generated on the device (input generation for tests and
+ * serving benchmarks; none of the smoother's arithmetic).  Fills F, H, K (n x n), G (m x n),
+ * C (m x m) -- one matrix each, to be passed with time_invariant = all KS_TI_* bits -- and
+ * o ([k][m] per step), all device pointers, from a counter-based generator keyed by `seed`:
+ * F = f_scale * (product of three random Householder reflections), H = I, K and C = L L^T
+ * (L lower triangular, diagonal U[0.5, 1.5], off-diagonal N(0, 0.01)), G ~ N(0, 1/n),
+ * o ~ N(0, 1).
+ */
+ks_status ks_generate(ks_ctx *ctx, int64_t k, int n, int m, uint64_t seed, double f_scale,
+                      double *F, double *H, double *K, double *G, double *C, double *o);
+
+/*
+ * Serving loop (continuous batching; the paper has no counterpart).  A server owns a scheduler
+ * thread and a stream of the ctx's device.  Requests are admitted in arrival order as device
+ * memory (mem_budget) and slots (max_active) allow; every scheduler tick advances each admitted
+ * request by one stage of the method (whitening, one recursion level, the base, one level of
+ * back substitution, one refinement step, one SelInv level), and the requests at the same kind
+ * of stage share ONE launch per state-dimension group even when they are at different recursion
+ * depths, so work of requests that arrived at different times overlaps on the device.  A
+ * finished request's factor can be kept for later covariance queries.
+ */
+typedef struct ks_server ks_server;
+
+typedef struct {
+    size_t mem_budget;  /* device bytes for requests' work memory; 0 = 3/4 of the free memory */
+    int max_active;     /* most admitted requests at a time; 0 = 4096 */
+    int keep_factors;   /* 1 = keep every finished request's factor for ks_server_covariances */
+} ks_server_options;
+
+typedef struct {
+    int done;           /* 1 once the request finished (its outputs are written) */
+    int status;         /* ks_status of the request */
+    int64_t info;       /* failing index, -1 if none */
+    double queue_ms;    /* submission -> admission */
+    double latency_ms;  /* submission -> completion */
+    int64_t k;
+    int n;
+} ks_request_info;
+
+typedef struct {
+    int64_t submitted, admitted, completed, active, queued;
+    int64_t ticks, launches;
+    size_t bytes_in_use, bytes_budget;
+} ks_server_counters;
+
+ks_status ks_server_create(ks_ctx *ctx, const ks_server_options *opt, ks_server **out);
+/* Enqueues one problem (arrays as in ks_smooth_batch; they must stay valid until the request is
+ * done).  Never blocks on the GPU.  *id receives the request id. */
+ks_status ks_server_submit(ks_server *srv, const ks_problem *prob, int64_t *id);
+/* Enqueues a synthetic problem generated on the device at admission (see ks_generate, f_scale
+ * 0.99); its outputs stay in server memory (fetch with ks_server_result). */
+ks_status ks_server_submit_synthetic(ks_server *srv, int64_t k, int n, int m, uint64_t seed,
+                                     int want_cov, int64_t *id);
+/* Covariance follow-up on a finished request whose factor was kept: enqueues the SelInv levels
+ * on that factor; cov_out (device or host, [k][n][n]) or NULL (keep them in server memory). */
+ks_status ks_server_covariances(ks_server *srv, int64_t id, double *cov_out, int64_t *follow_id);
+/* Waits up to timeout_ms (< 0: forever) for request id; fills *out (may be NULL). */
+ks_status ks_server_wait(ks_server *srv, int64_t id, double timeout_ms, ks_request_info *out);
+/* Copies a finished request's states / covariances kept in server memory (either may be NULL). */
+ks_status ks_server_result(ks_server *srv, int64_t id, double *u_out, double *cov_out);
+/* Frees a finished request's kept memory (factor, outputs). */
+ks_status ks_server_release(ks_server *srv, int64_t id);
+ks_status ks_server_stats(ks_server *srv, ks_server_counters *out);
+/* Finishes every admitted and queued request, then frees the server. */
+ks_status ks_server_destroy(ks_server *srv);
 
 /*
  * Covariances of the smoothed states, cov(u_hat_i) = [(R^T R)^{-1}]_{ii}, by the odd-even

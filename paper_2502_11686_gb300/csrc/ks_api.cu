@@ -222,7 +222,8 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     }
     }
 
-    WhitenArgs wa;
+    WhitenArgs wa{};
+    wa.ti = 0;
     wa.k = k;
     wa.n = n;
     wa.mmax = mmax;
@@ -269,13 +270,14 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
             for (int l = L; l >= 0; --l) KS_CUDA(ctx, sops->backsub(k, l, R, nullptr, u, fp32, st));
         } else {
             KS_CUDA(ctx, launch_base(n, k, L, bufs[cur], R, wa.cn2, wa.cd2, ctx->d_bad, fp32, st));
-            for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_backsub(n, k, l, R, nullptr, u, fp32, st));
+            for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_backsub_warp(n, k, l, R, fp32, u, st));
         }
     }
 
     if (fp32) {
         Phase ph(ctx, KS_PHASE_REFINE);
-        RefineArgs ra;
+        RefineArgs ra{};
+        ra.ti = 0;
         ra.k = k;
         ra.n = n;
         ra.m_uniform = wa.m_uniform;
@@ -293,10 +295,7 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
             // FP32 correction solve; the scratch vectors reuse the FP64 ones' space.
             KS_CUDA(ctx, sops->refine(ra, (float*)ra.q, (float*)ra.g, (float*)w, (float*)d, R, L, st));
         } else {
-            KS_CUDA(ctx, launch_refine_gradient(ra, st));
-            for (int l = 0; l <= L; ++l) KS_CUDA(ctx, launch_rt_solve(n, k, l, R, ra.g, w, fp32, st));
-            for (int l = L; l >= 0; --l) KS_CUDA(ctx, launch_backsub(n, k, l, R, w, d, fp32, st));
-            KS_CUDA(ctx, launch_axpy(u, d, k * n, st));
+            KS_CUDA(ctx, launch_refine_warp(ra, (float*)ra.q, (float*)ra.g, (float*)w, (float*)d, R, L, st));
         }
     }
     if (!u_dev) {

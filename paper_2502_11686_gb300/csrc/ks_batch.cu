@@ -125,6 +125,8 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
             uni = uni && mi == P.m[0];
         }
         if (t1 > 0 && (!P.G || !P.o || !P.C)) return fail(ctx, KS_ERR_ARG, "problem %d: G, o, C needed", p);
+        if ((P.time_invariant & (KS_TI_G | KS_TI_C)) && !uni)
+            return fail(ctx, KS_ERR_ARG, "problem %d: time-invariant G / C need the same m at every step", p);
         mmax[p] = mm;
         m0[p] = P.m[0];
         uniform[p] = uni;
@@ -163,8 +165,11 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
         const int64_t RS = small ? nt + 2 * nn + n : rstore_rs((int)n);
         Mem& M = mem[p];
         const double* src[7] = {P.F, P.H, P.c, P.K, P.G, P.o, P.C};
-        const size_t cnt[7] = {(size_t)(ke * nn), (size_t)(ke * nn), (size_t)(ke * n), (size_t)(ke * nn),
-                               (size_t)(tot_m[p] * n), (size_t)tot_m[p], (size_t)tot_m2[p]};
+        const unsigned ti = P.time_invariant;
+        const int64_t kf = (ti & KS_TI_F) ? 1 : ke, kh = (ti & KS_TI_H) ? 1 : ke, kk = (ti & KS_TI_K) ? 1 : ke;
+        const size_t cnt[7] = {(size_t)(kf * nn), (size_t)(kh * nn), (size_t)(ke * n), (size_t)(kk * nn),
+                               (size_t)((ti & KS_TI_G) ? (int64_t)m0[p] * n : tot_m[p] * n), (size_t)tot_m[p],
+                               (size_t)((ti & KS_TI_C) ? (int64_t)m0[p] * m0[p] : tot_m2[p])};
         for (int a = 0; a < 7; ++a)
             M.stage[a] = (src[a] && cnt[a] && !is_device_ptr(src[a])) ? plan.take(cnt[a] * sizeof(double)) + 1 : 0;
         M.m = M.goff = M.coff = 0;
@@ -218,8 +223,12 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
             const double* src[7] = {P.F, P.H, P.c, P.K, P.G, P.o, P.C};
             const double* dst[7];
             const int64_t ke = P.k > 1 ? P.k - 1 : 0, nn = (int64_t)P.n * P.n;
-            const size_t cnt[7] = {(size_t)(ke * nn), (size_t)(ke * nn), (size_t)(ke * P.n), (size_t)(ke * nn),
-                                   (size_t)(tot_m[p] * P.n), (size_t)tot_m[p], (size_t)tot_m2[p]};
+            const unsigned ti = P.time_invariant;
+            const int64_t kf = (ti & KS_TI_F) ? 1 : ke, kh = (ti & KS_TI_H) ? 1 : ke, kk = (ti & KS_TI_K) ? 1 : ke;
+            const size_t cnt[7] = {(size_t)(kf * nn), (size_t)(kh * nn), (size_t)(ke * P.n), (size_t)(kk * nn),
+                                   (size_t)((ti & KS_TI_G) ? (int64_t)m0[p] * P.n : tot_m[p] * P.n), (size_t)tot_m[p],
+                                   (size_t)((ti & KS_TI_C) ? (int64_t)m0[p] * m0[p] : tot_m2[p])};
+            D.ti = ti;
             for (int a = 0; a < 7; ++a) {
                 if (M.stage[a]) {
                     KS_CUDA(ctx, cudaMemcpyAsync(ws + M.stage[a] - 1, src[a], cnt[a] * sizeof(double),
@@ -381,7 +390,23 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
     for (const Group& g : groups)
         if (!ctx->tuned.count(g.sig(fp32)) && g.L >= 1) tuning = true;
     ctx->prof.calls++;
-    if (tuning || !ctx->shapes_seen.count(shape_key())) {
+    auto op_phase = [](int op) {
+        switch (op) {
+            case B_WHITEN: return (int)KS_PHASE_WHITEN;
+            case B_LEVEL: return (int)KS_PHASE_LEVEL;
+            case B_BASE:
+            case B_BACKSUB: return (int)KS_PHASE_BACKSUB;
+            case B_SELINV: return (int)KS_PHASE_SELINV;
+            default: return (int)KS_PHASE_REFINE;
+        }
+    };
+    if (ctx->profile && !tuning) {
+        // Profiling: the same launches issued one by one, each timed into its phase.
+        for (const Launch& l : launches) {
+            Phase ph(ctx, op_phase(l.op));
+            KS_CUDA(ctx, issue(l, grid_of(groups[l.group], l.op)));
+        }
+    } else if (tuning || !ctx->shapes_seen.count(shape_key())) {
         Phase ph(ctx, KS_PHASE_BATCH);
         cudaEvent_t e0 = get_event(ctx), e1 = get_event(ctx);
         for (size_t i = 0; i < launches.size(); ++i) {

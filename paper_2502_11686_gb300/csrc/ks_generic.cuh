@@ -6,17 +6,21 @@
 
 namespace ks {
 
-// One step of the column-owner whitening: every thread of the block must call it.
+// One step of the column-owner whitening: every thread of the block must call it.  The two
+// Cholesky factorizations run in FP64; the triangular solves and the QR of the observation block
+// run in the working precision T (the smem slots are sized for doubles either way).
 template <typename T>
 __device__ void whiten_cta_step(const WhitenArgs& a, int64_t i, double* sm) {
     const int n = a.n;
     const WhitenLayout L = whiten_layout(n, a.mmax);
     double* KC = sm + L.kc;
-    double* W = sm + L.w;
+    T* W = reinterpret_cast<T*>(sm + L.w);
     double* OC = sm + L.oc;
-    double* Gm = sm + L.g;
-    double* Tt = sm + L.t;
-    double* scal = sm + L.scal;
+    T* Gm = reinterpret_cast<T*>(sm + L.g);
+    T* Tt = reinterpret_cast<T*>(sm + L.t);
+    T* scal = reinterpret_cast<T*>(sm + L.scal);
+    T* KT = reinterpret_cast<T*>(sm + L.kt);
+    T* OT = reinterpret_cast<T*>(sm + L.ot);
     const int tid = threadIdx.x, nth = blockDim.x;
     const int64_t CS = level_cs(n);
     T* out = reinterpret_cast<T*>(a.level0);
@@ -35,27 +39,27 @@ __device__ void whiten_cta_step(const WhitenArgs& a, int64_t i, double* sm) {
     const bool hasE = (i + 1 < a.k);
     // ---- loads (coalesced over the row-major source blocks) ----
     if (hasE) {
-        const double* Ki = a.K + i * (int64_t)n * n;
-        const double* Fi = a.F + i * (int64_t)n * n;
-        const double* Hi = a.H + i * (int64_t)n * n;
+        const double* Ki = a.K + ti_step(a.ti, TI_K, i) * (int64_t)n * n;
+        const double* Fi = a.F + ti_step(a.ti, TI_F, i) * (int64_t)n * n;
+        const double* Hi = a.H + ti_step(a.ti, TI_H, i) * (int64_t)n * n;
         for (int e = tid; e < n * n; e += nth) {
             int r = e / n, c = e - r * n;
             KC[r * L.ldk + c] = Ki[e];
-            W[r * L.ldw + c] = -Fi[e];
-            W[r * L.ldw + n + c] = Hi[e];
+            W[r * L.ldw + c] = (T)(-Fi[e]);
+            W[r * L.ldw + n + c] = (T)Hi[e];
         }
-        for (int r = tid; r < n; r += nth) W[r * L.ldw + 2 * n] = a.c ? a.c[i * n + r] : 0.0;
+        for (int r = tid; r < n; r += nth) W[r * L.ldw + 2 * n] = a.c ? (T)a.c[i * n + r] : T(0);
     }
     for (int e = tid; e < mi * mi; e += nth) {
         int r = e / mi, c = e - r * mi;
-        OC[r * L.ldo + c] = a.C[co + e];
+        OC[r * L.ldo + c] = a.C[((a.ti & TI_C) ? 0 : co) + e];
     }
     for (int e = tid; e < mi * n; e += nth) {
         int r = e / n, c = e - r * n;
-        Gm[r * L.ldg + c] = a.G[go * n + e];
+        Gm[r * L.ldg + c] = (T)a.G[((a.ti & TI_G) ? 0 : go) * n + e];
     }
-    for (int r = tid; r < mi; r += nth) Gm[r * L.ldg + n] = a.o[go + r];
-    for (int e = tid; e < n * L.ldt; e += nth) Tt[e] = 0.0;
+    for (int r = tid; r < mi; r += nth) Gm[r * L.ldg + n] = (T)a.o[go + r];
+    for (int e = tid; e < n * L.ldt; e += nth) Tt[e] = T(0);
     __syncthreads();
 
     // ---- Cholesky of K_i (threads [0,n)) and C_i (threads [n, n+mi)), right-looking,
@@ -89,19 +93,30 @@ __device__ void whiten_cta_step(const WhitenArgs& a, int64_t i, double* sm) {
         __syncthreads();
     }
 
+    // ---- working-precision copies of the factors ----
+    for (int e = tid; e < nK * nK; e += nth) {
+        int r = e / nK, c = e - r * nK;
+        KT[r * L.ldk + c] = (T)KC[r * L.ldk + c];
+    }
+    for (int e = tid; e < mi * mi; e += nth) {
+        int r = e / mi, c = e - r * mi;
+        OT[r * L.ldo + c] = (T)OC[r * L.ldo + c];
+    }
+    __syncthreads();
+
     // ---- forward substitution: W <- L_K^{-1} W (2n+1 columns), Gm <- L_C^{-1} Gm ----
     {
-        double* B = nullptr;
-        const double* Lf = nullptr;
+        T* B = nullptr;
+        const T* Lf = nullptr;
         int ldb = 0, ldl = 0, dim2 = 0;
         if (tid < 2 * n + 1) {
-            if (hasE) { B = W + tid; ldb = L.ldw; Lf = KC; ldl = L.ldk; dim2 = n; }
+            if (hasE) { B = W + tid; ldb = L.ldw; Lf = KT; ldl = L.ldk; dim2 = n; }
         } else if (tid < 3 * n + 2) {
-            if (mi > 0) { B = Gm + (tid - 2 * n - 1); ldb = L.ldg; Lf = OC; ldl = L.ldo; dim2 = mi; }
+            if (mi > 0) { B = Gm + (tid - 2 * n - 1); ldb = L.ldg; Lf = OT; ldl = L.ldo; dim2 = mi; }
         }
         if (B != nullptr) {
             for (int r = 0; r < dim2; ++r) {
-                double s = B[r * ldb];
+                T s = B[r * ldb];
                 for (int q = 0; q < r; ++q) s = fma(-Lf[r * ldl + q], B[q * ldb], s);
                 B[r * ldb] = s / Lf[r * ldl + r];
             }
@@ -112,25 +127,25 @@ __device__ void whiten_cta_step(const WhitenArgs& a, int64_t i, double* sm) {
     // ---- reduce the observation block: QR of [0 (n x n) ; Chat (mi x n)] with its rhs ----
     {
         const int fcol = (tid < n) ? tid : -1;
-        double* ctop = (tid == n) ? (Tt + n) : nullptr;
-        double* cbot = (tid == n) ? (Gm + n) : nullptr;
-        tpqrt_columns<double>(n, mi, Tt, L.ldt, Gm, L.ldg, fcol, ctop, L.ldt, cbot, L.ldg, scal);
+        T* ctop = (tid == n) ? (Tt + n) : nullptr;
+        T* cbot = (tid == n) ? (Gm + n) : nullptr;
+        tpqrt_columns<T>(n, mi, Tt, L.ldt, Gm, L.ldg, fcol, ctop, L.ldt, cbot, L.ldg, scal);
     }
 
     // ---- stores ----
     T* rec = out + i * CS;
     for (int e = tid; e < n * n; e += nth) {
         int r = e / n, c = e - r * n;
-        rec[e] = (T)(c >= r ? Tt[r * L.ldt + c] : 0.0);
+        rec[e] = c >= r ? Tt[r * L.ldt + c] : T(0);
     }
-    for (int r = tid; r < n; r += nth) rec[n * n + r] = (T)Tt[r * L.ldt + n];
+    for (int r = tid; r < n; r += nth) rec[n * n + r] = Tt[r * L.ldt + n];
     if (hasE) {
         T* nxt = out + (i + 1) * CS + (int64_t)n * n + n;
         for (int e = tid; e < 2 * n * n; e += nth) {
             int r = e / (2 * n), c = e - r * 2 * n;
-            nxt[e] = (T)W[r * L.ldw + c];
+            nxt[e] = W[r * L.ldw + c];
         }
-        for (int r = tid; r < n; r += nth) nxt[2 * n * n + r] = (T)W[r * L.ldw + 2 * n];
+        for (int r = tid; r < n; r += nth) nxt[2 * n * n + r] = W[r * L.ldw + 2 * n];
         if (a.LK != nullptr) {
             double* lk = a.LK + i * (int64_t)n * n;
             for (int e = tid; e < n * n; e += nth) {
@@ -147,17 +162,17 @@ __device__ void whiten_cta_step(const WhitenArgs& a, int64_t i, double* sm) {
     }
     if (tid == 0) {
         double s = 0.0;
-        for (int r = 0; r < mi; ++r) s = fma(Gm[r * L.ldg + n], Gm[r * L.ldg + n], s);
+        for (int r = 0; r < mi; ++r) s = fma((double)Gm[r * L.ldg + n], (double)Gm[r * L.ldg + n], s);
         a.resid[i] = s;
     }
     // Column norms^2 of U A for state i (Chat_i and B_i) and state i+1 (D_i).
     for (int col = tid; col < n; col += nth) {
         double sc = 0.0, sb = 0.0, sd = 0.0;
-        for (int r = 0; r <= col; ++r) sc = fma(Tt[r * L.ldt + col], Tt[r * L.ldt + col], sc);
+        for (int r = 0; r <= col; ++r) sc = fma((double)Tt[r * L.ldt + col], (double)Tt[r * L.ldt + col], sc);
         if (hasE) {
             for (int r = 0; r < n; ++r) {
-                sb = fma(W[r * L.ldw + col], W[r * L.ldw + col], sb);
-                sd = fma(W[r * L.ldw + n + col], W[r * L.ldw + n + col], sd);
+                sb = fma((double)W[r * L.ldw + col], (double)W[r * L.ldw + col], sb);
+                sd = fma((double)W[r * L.ldw + n + col], (double)W[r * L.ldw + n + col], sd);
             }
             a.cd2[(i + 1) * n + col] = sd;
         }

@@ -57,7 +57,7 @@ __host__ __device__ inline TileLayout tile_layout(int n) {
 // Shared-memory layout of the whitening of one step (elements of double).
 struct WhitenLayout {
     int n, m, ldk, ldw, ldo, ldg, ldt;
-    int kc, w, oc, g, t, top, scal, total;
+    int kc, w, oc, g, t, top, scal, kt, ot, total;
 };
 
 __host__ __device__ inline WhitenLayout whiten_layout(int n, int m) {
@@ -76,7 +76,9 @@ __host__ __device__ inline WhitenLayout whiten_layout(int n, int m) {
     L.t = L.g + m * L.ldg;
     L.top = L.t;  // alias: the rhs column of the top block is column n of t
     L.scal = L.t + n * L.ldt;
-    L.total = L.scal + 2 * n;
+    L.kt = L.scal + 2 * n;       // working-precision copies of the two Cholesky factors
+    L.ot = L.kt + n * L.ldk;
+    L.total = L.ot + m * L.ldo;
     return L;
 }
 
@@ -181,7 +183,16 @@ struct SoaIO {
 // add the number of kernels they launched to t_launches (the calling thread's counter).
 extern thread_local uint64_t t_launches;
 
+// Time-invariant inputs: a set bit means the array holds ONE matrix used at every step (stride
+// 0); the kernels still read it for every step.  G and C may be time invariant only when every
+// step has the same observation count.
+enum { TI_F = 1, TI_H = 2, TI_K = 4, TI_G = 8, TI_C = 16 };
+__host__ __device__ __forceinline__ int64_t ti_step(unsigned ti, unsigned bit, int64_t i) {
+    return (ti & bit) ? 0 : i;
+}
+
 struct WhitenArgs {
+    unsigned ti;                  // TI_* bits
     int64_t k;
     int n, mmax, m_uniform;       // m_uniform >= 0: every m_i equals it; -1: use goff/coff
     const int32_t* m;             // device [k] (m_uniform < 0)
@@ -251,6 +262,7 @@ cudaError_t launch_sum(const double* x, int64_t count, double* out, cudaStream_t
 // Refinement (KS_FP32_REFINE).  g = (UA)^T U (b - A u) in FP64 (Section 2's normal equations
 // of the whitened system), then R^T w = g level by level, then R d = w, u += d.
 struct RefineArgs {
+    unsigned ti;
     int64_t k;
     int n, m_uniform;
     const int32_t* m;
@@ -265,6 +277,12 @@ cudaError_t launch_rt_solve(int n, int64_t k, int level, const void* R, double* 
                             bool fp32, cudaStream_t st);
 cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t st);
 
+// Warp-per-unit back substitution and mixed-precision refinement of the column-owner path.
+cudaError_t launch_backsub_warp(int n, int64_t k, int level, const void* R, bool fp32,
+                                double* u, cudaStream_t st);
+cudaError_t launch_refine_warp(const RefineArgs& a, float* q, float* g, float* w, float* d,
+                               const void* R, int L, cudaStream_t st);
+
 // ---------------------------------------------------------------------------------------------
 // Batched problems.  Every problem of a batch has a descriptor in device memory; a launch
 // covers the units (steps, tiles, rows ...) of all problems of one class (same n and path) at
@@ -272,6 +290,8 @@ cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t 
 // descriptors and work lists live at fixed device addresses, so a captured CUDA graph of the
 // launch sequence can be replayed for any batch of the same shape.
 struct ProbDesc {
+    unsigned ti;
+    int cur_level;                // serving: this problem's level in the current launch
     int64_t k;
     int n, m_uniform, mmax, L;
     const int32_t* m;
@@ -294,8 +314,12 @@ struct BatchWork {
     const int* probs;      // the problems of this launch's class
     const int64_t* off;    // prefix sum of units per problem [np + 1]
     int np;
-    int level;
+    int level;             // >= 0: the level of every problem; -1: each problem's cur_level
 };
+
+__device__ __forceinline__ int work_level(const BatchWork& w, const ProbDesc& P) {
+    return w.level >= 0 ? w.level : P.cur_level;
+}
 
 // Index into probs of the problem owning global unit u (off[p] <= u < off[p+1]).
 __device__ __forceinline__ int batch_find(const int64_t* off, int np, int64_t u) {
@@ -309,6 +333,7 @@ __device__ __forceinline__ int batch_find(const int64_t* off, int np, int64_t u)
 
 __device__ __forceinline__ WhitenArgs whiten_args_of(const ProbDesc& P) {
     WhitenArgs a;
+    a.ti = P.ti;
     a.k = P.k; a.n = P.n; a.mmax = P.mmax; a.m_uniform = P.m_uniform;
     a.m = P.m; a.goff = P.goff; a.coff = P.coff;
     a.F = P.F; a.H = P.H; a.c = P.c; a.K = P.K; a.G = P.G; a.o = P.o; a.C = P.C;
@@ -319,6 +344,7 @@ __device__ __forceinline__ WhitenArgs whiten_args_of(const ProbDesc& P) {
 
 __device__ __forceinline__ RefineArgs refine_args_of(const ProbDesc& P) {
     RefineArgs a;
+    a.ti = P.ti;
     a.k = P.k; a.n = P.n; a.m_uniform = P.m_uniform; a.m = P.m; a.goff = P.goff; a.coff = P.coff;
     a.F = P.F; a.H = P.H; a.c = P.c; a.G = P.G; a.o = P.o; a.LK = P.LK; a.LC = P.LC;
     a.u = P.u; a.g = (double*)P.g; a.q = (double*)P.q;

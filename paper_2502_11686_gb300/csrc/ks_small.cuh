@@ -150,7 +150,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
     for (int c = 0; c < N; ++c) cb2[c] = 0.0;
     if (i + 1 < k) {
         // K_i = L L^T in FP64.
-        const double* Ki = a.K + i * N * N;
+        const double* Ki = a.K + ti_step(a.ti, TI_K, i) * N * N;
         double L[N][N];
 #pragma unroll
         for (int r = 0; r < N; ++r)
@@ -191,8 +191,8 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
         }
         // [-B | D | rE] = L^{-1} [-F | H | c], column by column (FP64 mode in double, refine
         // mode in FP32 from the FP64 factor).
-        const double* Fi = a.F + i * N * N;
-        const double* Hi = a.H + i * N * N;
+        const double* Fi = a.F + ti_step(a.ti, TI_F, i) * N * N;
+        const double* Hi = a.H + ti_step(a.ti, TI_H, i) * N * N;
         double cd2[N];
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
@@ -245,7 +245,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
     }
     double res = 0.0;
     if (mi > 0) {
-        const double* Ci = a.C + co;
+        const double* Ci = a.C + ((a.ti & TI_C) ? 0 : co);
         double Lo[N][N];
 #pragma unroll
         for (int r = 0; r < N; ++r)
@@ -279,7 +279,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
                     if (r < mi && c < mi) a.LC[co + r * mi + c] = c <= r ? Lo[r][c] : 0.0;
         }
         T M[N][N], ob[N];
-        const double* Gi = a.G + go * N;
+        const double* Gi = a.G + ((a.ti & TI_G) ? 0 : go) * N;
         const double* oi = a.o + go;
 #pragma unroll
         for (int r = 0; r < N; ++r) {
@@ -772,8 +772,8 @@ __device__ void selinv_row(int64_t k, int level, int64_t q, const T* R, T* Sx, d
 // q_i = K_i^{-1} e_i with e_i = F_i u_i + c_i - H_i u_{i+1} (e in FP64, the solve in FP32).
 template <int N>
 __device__ void refine_q_step(const RefineArgs& a, int64_t i, float* q) {
-    const double* F = a.F + i * N * N;
-    const double* H = a.H + i * N * N;
+    const double* F = a.F + ti_step(a.ti, TI_F, i) * N * N;
+    const double* H = a.H + ti_step(a.ti, TI_H, i) * N * N;
     const double* Lk = a.LK + i * N * N;
     double u0[N], u1[N];
 #pragma unroll
@@ -821,7 +821,7 @@ __device__ void refine_g_col(const RefineArgs& a, int64_t c, const float* q, flo
 #pragma unroll
     for (int r = 0; r < N; ++r) acc[r] = 0.f;
     if (c >= 1) {
-        const double* H = a.H + (c - 1) * N * N;
+        const double* H = a.H + ti_step(a.ti, TI_H, c - 1) * N * N;
         float qv[N];
 #pragma unroll
         for (int p = 0; p < N; ++p) qv[p] = q[(c - 1) * N + p];
@@ -831,7 +831,7 @@ __device__ void refine_g_col(const RefineArgs& a, int64_t c, const float* q, flo
             for (int r = 0; r < N; ++r) acc[r] = fmaf((float)H[p * N + r], qv[p], acc[r]);
     }
     if (c + 1 < a.k) {
-        const double* F = a.F + c * N * N;
+        const double* F = a.F + ti_step(a.ti, TI_F, c) * N * N;
         float qv[N];
 #pragma unroll
         for (int p = 0; p < N; ++p) qv[p] = q[c * N + p];
@@ -852,7 +852,7 @@ __device__ void refine_g_col(const RefineArgs& a, int64_t c, const float* q, flo
         co = a.coff[c];
     }
     if (mi > 0) {
-        const double* G = a.G + go * N;
+        const double* G = a.G + ((a.ti & TI_G) ? 0 : go) * N;
         const double* Lc = a.LC + co;
         double uc[N];
 #pragma unroll

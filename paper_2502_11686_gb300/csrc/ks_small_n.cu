@@ -153,12 +153,12 @@ __global__ void __launch_bounds__(BLK) batch_k(const BatchWork* wk) {
     const Stash<T> st{reinterpret_cast<T*>(smem_raw), BLK, (int)threadIdx.x};
     const BatchWork w = *wk;
     const int64_t total = w.off[w.np];
-    const int l = w.level;
     for (int64_t u = blockIdx.x * (int64_t)BLK + threadIdx.x; u < total;
          u += (int64_t)gridDim.x * BLK) {
         const int pi = batch_find(w.off, w.np, u);
         const ProbDesc& P = w.desc[w.probs[pi]];
         const int64_t x = u - w.off[pi];
+        const int l = work_level(w, P);
         if constexpr (OP == B_WHITEN) {
             whiten_step<T, NN>(whiten_args_of(P), x, reinterpret_cast<T*>(P.lvl[0]));
         } else if constexpr (OP == B_LEVEL) {

@@ -219,8 +219,8 @@ __global__ void sum_kernel(const double* __restrict__ x, int64_t count, double* 
 __device__ void refine_q_generic(const RefineArgs& a, int64_t i) {
     if (i + 1 >= a.k) return;
     const int n = a.n, nn = n * n;
-    const double* F = a.F + i * nn;
-    const double* H = a.H + i * nn;
+    const double* F = a.F + ti_step(a.ti, TI_F, i) * nn;
+    const double* H = a.H + ti_step(a.ti, TI_H, i) * nn;
     const double* Lk = a.LK + i * nn;
     const double* u0 = a.u + i * n;
     const double* u1 = a.u + (i + 1) * n;
@@ -255,13 +255,13 @@ __device__ void refine_g_generic(const RefineArgs& a, int64_t c) {
     double g[KS_NMAX];
     for (int r = 0; r < n; ++r) g[r] = 0.0;
     if (c >= 1) {
-        const double* H = a.H + (c - 1) * nn;
+        const double* H = a.H + ti_step(a.ti, TI_H, c - 1) * nn;
         const double* qv = a.q + (c - 1) * n;
         for (int r = 0; r < n; ++r)
             for (int p = 0; p < n; ++p) g[r] = fma(H[p * n + r], qv[p], g[r]);
     }
     if (c + 1 < a.k) {
-        const double* F = a.F + c * nn;
+        const double* F = a.F + ti_step(a.ti, TI_F, c) * nn;
         const double* qv = a.q + c * n;
         for (int r = 0; r < n; ++r)
             for (int p = 0; p < n; ++p) g[r] = fma(-F[p * n + r], qv[p], g[r]);
@@ -278,7 +278,7 @@ __device__ void refine_g_generic(const RefineArgs& a, int64_t c) {
         co = a.coff[c];
     }
     if (mi > 0) {
-        const double* G = a.G + go * n;
+        const double* G = a.G + ((a.ti & TI_G) ? 0 : go) * n;
         const double* Lc = a.LC + co;
         const double* uc = a.u + c * n;
         double v[KS_NMAX];
@@ -462,21 +462,304 @@ cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t 
     return cudaGetLastError();
 }
 
+// ---- warp-per-unit kernels of the column-owner path -----------------------------------------
+// One warp per block row / column / step; lane l owns rows l and l+32 (n <= 64).  Triangular
+// substitutions proceed one unknown at a time: its owner lane divides and broadcasts it with a
+// shuffle, and every lane updates its own rows.  In FP32 + refinement mode the vectors are FP32
+// except the residuals of the refinement, which are formed in FP64.
+
+// Back substitution of block row q at `level`: u_c = Rd^{-1}(rhs - Rl u_a - Rr u_b).
+// rhs = y from the R store (w == nullptr) or w_c.  Vectors of type TV, output of type TO.
+template <typename TR, typename TV, typename TO>
+__device__ void backsub_warp(int n, int64_t k, int level, int64_t q, const TR* __restrict__ R,
+                             const TV* __restrict__ w, TO* __restrict__ u) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = ((2 * q + 1) << level) - 1;
+    if (c >= k) return;
+    const int nn = n * n;
+    const TR* Rc = R + c * rstore_rs(n);
+    const int64_t a = c - (1LL << level), b = c + (1LL << level);
+    TV r0 = TV(0), r1 = TV(0);
+    const int i0 = lane, i1 = lane + 32;
+    if (i0 < n) r0 = w ? w[c * n + i0] : (TV)Rc[3 * nn + i0];
+    if (i1 < n) r1 = w ? w[c * n + i1] : (TV)Rc[3 * nn + i1];
+    if (a >= 0) {
+        for (int p = 0; p < n; ++p) {
+            const TV up = (TV)u[a * n + p];
+            if (i0 < n) r0 = fma(-(TV)Rc[nn + i0 * n + p], up, r0);
+            if (i1 < n) r1 = fma(-(TV)Rc[nn + i1 * n + p], up, r1);
+        }
+    }
+    if (b < k) {
+        for (int p = 0; p < n; ++p) {
+            const TV up = (TV)u[b * n + p];
+            if (i0 < n) r0 = fma(-(TV)Rc[2 * nn + i0 * n + p], up, r0);
+            if (i1 < n) r1 = fma(-(TV)Rc[2 * nn + i1 * n + p], up, r1);
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        TV x = TV(0);
+        if ((i & 31) == lane) x = ((i < 32) ? r0 : r1) / (TV)Rc[i * n + i];
+        x = __shfl_sync(0xffffffffu, x, i & 31);
+        if (i0 < i) r0 = fma(-(TV)Rc[i0 * n + i], x, r0);
+        if (i1 < i) r1 = fma(-(TV)Rc[i1 * n + i], x, r1);
+        if (i0 == i) r0 = x;
+        if (i1 == i) r1 = x;
+    }
+    if (i0 < n) u[c * n + i0] = (TO)r0;
+    if (i1 < n) u[c * n + i1] = (TO)r1;
+}
+
+// R^T w = g at `level` for alive column j (pull the two rows eliminated at level-1 that touch
+// it, then solve with Rd^T if it is eliminated here).
+template <typename TR, typename TV>
+__device__ void rt_solve_warp(int n, int64_t k, int level, int64_t j, const TR* __restrict__ R,
+                              TV* __restrict__ g, TV* __restrict__ w) {
+    const int lane = threadIdx.x & 31;
+    if (j >= (k >> level)) return;
+    const int64_t c = ((j + 1) << level) - 1;
+    const int nn = n * n;
+    const int64_t RS = rstore_rs(n);
+    const int i0 = lane, i1 = lane + 32;
+    TV r0 = i0 < n ? g[c * n + i0] : TV(0), r1 = i1 < n ? g[c * n + i1] : TV(0);
+    if (level >= 1) {
+        const int64_t h = 1LL << (level - 1);
+        if (c - h >= 0) {
+            const TR* Rr = R + (c - h) * RS + 2 * nn;
+            const TV* wr = w + (c - h) * n;
+            for (int p = 0; p < n; ++p) {
+                const TV wp = wr[p];
+                if (i0 < n) r0 = fma(-(TV)Rr[p * n + i0], wp, r0);
+                if (i1 < n) r1 = fma(-(TV)Rr[p * n + i1], wp, r1);
+            }
+        }
+        if (c + h < k) {
+            const TR* Rl = R + (c + h) * RS + nn;
+            const TV* wr = w + (c + h) * n;
+            for (int p = 0; p < n; ++p) {
+                const TV wp = wr[p];
+                if (i0 < n) r0 = fma(-(TV)Rl[p * n + i0], wp, r0);
+                if (i1 < n) r1 = fma(-(TV)Rl[p * n + i1], wp, r1);
+            }
+        }
+    }
+    if (ctz64(c + 1) == level) {
+        const TR* Rd = R + c * RS;
+        for (int i = 0; i < n; ++i) {
+            TV x = TV(0);
+            if ((i & 31) == lane) x = ((i < 32) ? r0 : r1) / (TV)Rd[i * n + i];
+            x = __shfl_sync(0xffffffffu, x, i & 31);
+            if (i0 > i && i0 < n) r0 = fma(-(TV)Rd[i * n + i0], x, r0);
+            if (i1 > i && i1 < n) r1 = fma(-(TV)Rd[i * n + i1], x, r1);
+            if (i0 == i) r0 = x;
+            if (i1 == i) r1 = x;
+        }
+        if (i0 < n) w[c * n + i0] = r0;
+        if (i1 < n) w[c * n + i1] = r1;
+    } else {
+        if (i0 < n) g[c * n + i0] = r0;
+        if (i1 < n) g[c * n + i1] = r1;
+    }
+}
+
+// Warp-cooperative solves with an FP64 lower-triangular factor L (ld = dim), in type TV:
+// forward (L y = x) then backward (L^T z = y); x given per lane in rows lane, lane+32.
+template <typename TV>
+__device__ void llt_solve_warp(int dim, const double* __restrict__ Lf, TV& r0, TV& r1) {
+    const int lane = threadIdx.x & 31;
+    const int i0 = lane, i1 = lane + 32;
+    for (int i = 0; i < dim; ++i) {
+        TV x = TV(0);
+        if ((i & 31) == lane) x = ((i < 32) ? r0 : r1) / (TV)Lf[i * dim + i];
+        x = __shfl_sync(0xffffffffu, x, i & 31);
+        if (i0 > i && i0 < dim) r0 = fma(-(TV)Lf[i0 * dim + i], x, r0);
+        if (i1 > i && i1 < dim) r1 = fma(-(TV)Lf[i1 * dim + i], x, r1);
+        if (i0 == i) r0 = x;
+        if (i1 == i) r1 = x;
+    }
+    for (int i = dim - 1; i >= 0; --i) {
+        TV x = TV(0);
+        if ((i & 31) == lane) x = ((i < 32) ? r0 : r1) / (TV)Lf[i * dim + i];
+        x = __shfl_sync(0xffffffffu, x, i & 31);
+        if (i0 < i) r0 = fma(-(TV)Lf[i * dim + i0], x, r0);
+        if (i1 < i) r1 = fma(-(TV)Lf[i * dim + i1], x, r1);
+        if (i0 == i) r0 = x;
+        if (i1 == i) r1 = x;
+    }
+}
+
+// q_i = K_i^{-1} (F_i u_i + c_i - H_i u_{i+1}): the residual in FP64, the solve in TV.
+template <typename TV>
+__device__ void refine_q_warp(const RefineArgs& a, int64_t i, TV* __restrict__ q) {
+    if (i + 1 >= a.k) return;
+    const int lane = threadIdx.x & 31, n = a.n, nn = n * n;
+    const double* F = a.F + ti_step(a.ti, TI_F, i) * nn;
+    const double* H = a.H + ti_step(a.ti, TI_H, i) * nn;
+    double e0 = 0.0, e1 = 0.0;
+    const int i0 = lane, i1 = lane + 32;
+    if (i0 < n) e0 = a.c ? a.c[i * n + i0] : 0.0;
+    if (i1 < n) e1 = a.c ? a.c[i * n + i1] : 0.0;
+    for (int p = 0; p < n; ++p) {
+        const double u0 = a.u[i * n + p], u1 = a.u[(i + 1) * n + p];
+        if (i0 < n) e0 = fma(-H[i0 * n + p], u1, fma(F[i0 * n + p], u0, e0));
+        if (i1 < n) e1 = fma(-H[i1 * n + p], u1, fma(F[i1 * n + p], u0, e1));
+    }
+    TV r0 = (TV)e0, r1 = (TV)e1;
+    llt_solve_warp<TV>(n, a.LK + i * nn, r0, r1);
+    if (i0 < n) q[i * n + i0] = r0;
+    if (i1 < n) q[i * n + i1] = r1;
+}
+
+// g_c = H_{c-1}^T q_{c-1} - F_c^T q_c + G_c^T C_c^{-1} (o_c - G_c u_c), o - G u in FP64.
+template <typename TV>
+__device__ void refine_g_warp(const RefineArgs& a, int64_t c, const TV* __restrict__ q,
+                              TV* __restrict__ g) {
+    if (c >= a.k) return;
+    const int lane = threadIdx.x & 31, n = a.n, nn = n * n;
+    const int i0 = lane, i1 = lane + 32;
+    TV g0 = TV(0), g1 = TV(0);
+    if (c >= 1) {
+        const double* H = a.H + ti_step(a.ti, TI_H, c - 1) * nn;
+        for (int p = 0; p < n; ++p) {
+            const TV qp = q[(c - 1) * n + p];
+            if (i0 < n) g0 = fma((TV)H[p * n + i0], qp, g0);
+            if (i1 < n) g1 = fma((TV)H[p * n + i1], qp, g1);
+        }
+    }
+    if (c + 1 < a.k) {
+        const double* F = a.F + ti_step(a.ti, TI_F, c) * nn;
+        for (int p = 0; p < n; ++p) {
+            const TV qp = q[c * n + p];
+            if (i0 < n) g0 = fma(-(TV)F[p * n + i0], qp, g0);
+            if (i1 < n) g1 = fma(-(TV)F[p * n + i1], qp, g1);
+        }
+    }
+    int mi;
+    int64_t go, co;
+    if (a.m_uniform >= 0) {
+        mi = a.m_uniform;
+        go = c * mi;
+        co = c * (int64_t)mi * mi;
+    } else {
+        mi = a.m[c];
+        go = a.goff[c];
+        co = a.coff[c];
+    }
+    if (mi > 0) {
+        const double* G = a.G + ((a.ti & TI_G) ? 0 : go) * n;
+        double v0 = 0.0, v1 = 0.0;
+        if (i0 < mi) v0 = a.o[go + i0];
+        if (i1 < mi) v1 = a.o[go + i1];
+        for (int p = 0; p < n; ++p) {
+            const double up = a.u[c * n + p];
+            if (i0 < mi) v0 = fma(-G[i0 * n + p], up, v0);
+            if (i1 < mi) v1 = fma(-G[i1 * n + p], up, v1);
+        }
+        TV r0 = (TV)v0, r1 = (TV)v1;
+        llt_solve_warp<TV>(mi, a.LC + co, r0, r1);
+        for (int p = 0; p < mi; ++p) {
+            const TV vp = __shfl_sync(0xffffffffu, p < 32 ? r0 : r1, p & 31);
+            if (i0 < n) g0 = fma((TV)G[p * n + i0], vp, g0);
+            if (i1 < n) g1 = fma((TV)G[p * n + i1], vp, g1);
+        }
+    }
+    if (i0 < n) g[c * n + i0] = g0;
+    if (i1 < n) g[c * n + i1] = g1;
+}
+
+template <typename TR, typename TV, typename TO>
+__global__ void __launch_bounds__(128) backsub_warp_kernel(int n, int64_t k, int level, const TR* R,
+                                                           const TV* w, TO* u) {
+    const int64_t q = blockIdx.x * 4LL + (threadIdx.x >> 5);
+    if (q < (k >> level) - (k >> (level + 1))) backsub_warp<TR, TV, TO>(n, k, level, q, R, w, u);
+}
+
+template <typename TR, typename TV>
+__global__ void __launch_bounds__(128) rt_solve_warp_kernel(int n, int64_t k, int level, const TR* R,
+                                                            TV* g, TV* w) {
+    rt_solve_warp<TR, TV>(n, k, level, blockIdx.x * 4LL + (threadIdx.x >> 5), R, g, w);
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(128) refine_qg_warp_kernel(RefineArgs a, int which, TV* q, TV* g) {
+    const int64_t x = blockIdx.x * 4LL + (threadIdx.x >> 5);
+    if (which == 0) refine_q_warp<TV>(a, x, q);
+    else refine_g_warp<TV>(a, x, q, g);
+}
+
+template <typename TV>
+__global__ void add_kernel(double* __restrict__ u, const TV* __restrict__ d, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        u[i] += (double)d[i];
+}
+
+static unsigned warps_grid(int64_t units) {
+    int64_t b = (units + 3) / 4;
+    return (unsigned)(b < 1 ? 1 : (b > (1LL << 30) ? (1LL << 30) : b));
+}
+
+cudaError_t launch_backsub_warp(int n, int64_t k, int level, const void* R, bool fp32,
+                                double* u, cudaStream_t st) {
+    const int64_t rows = (k >> level) - (k >> (level + 1));
+    if (fp32)  // FP32 first solve; the refinement corrects it
+        backsub_warp_kernel<float, float, double><<<warps_grid(rows), 128, 0, st>>>(
+            n, k, level, (const float*)R, (const float*)nullptr, u);
+    else
+        backsub_warp_kernel<double, double, double><<<warps_grid(rows), 128, 0, st>>>(
+            n, k, level, (const double*)R, (const double*)nullptr, u);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refine_warp(const RefineArgs& a, float* q, float* g, float* w, float* d,
+                               const void* R, int L, cudaStream_t st) {
+    const int64_t k = a.k;
+    const float* Rf = static_cast<const float*>(R);
+    if (k > 1) {
+        refine_qg_warp_kernel<float><<<warps_grid(k - 1), 128, 0, st>>>(a, 0, q, g);
+        ++t_launches;
+    }
+    refine_qg_warp_kernel<float><<<warps_grid(k), 128, 0, st>>>(a, 1, q, g);
+    ++t_launches;
+    for (int l = 0; l <= L; ++l) {
+        rt_solve_warp_kernel<float, float><<<warps_grid(k >> l), 128, 0, st>>>(a.n, k, l, Rf, g, w);
+        ++t_launches;
+    }
+    for (int l = L; l >= 0; --l) {
+        backsub_warp_kernel<float, float, float><<<warps_grid((k >> l) - (k >> (l + 1))), 128, 0, st>>>(
+            a.n, k, l, Rf, w, d);
+        ++t_launches;
+    }
+    const int64_t cnt = k * a.n;
+    int64_t b = (cnt + 255) / 256;
+    add_kernel<float><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, st>>>(
+        const_cast<double*>(a.u), d, cnt);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
 // ---- batched column-owner launches ----------------------------------------------------------
 template <typename T, int OP>
 __global__ void __launch_bounds__(256) batch_generic_k(const BatchWork* wk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const BatchWork w = *wk;
     const int64_t total = w.off[w.np];
-    const int l = w.level;
     constexpr bool per_block = (OP == B_WHITEN || OP == B_LEVEL || OP == B_BASE || OP == B_SELINV);
-    const int64_t first = per_block ? blockIdx.x : blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t stride = per_block ? gridDim.x : (int64_t)gridDim.x * blockDim.x;
+    constexpr bool per_warp = (OP == B_BACKSUB || OP == B_REFINE_Q || OP == B_REFINE_G ||
+                               OP == B_RT_SOLVE || OP == B_BACKSUB_W);
+    const int64_t first = per_block ? blockIdx.x
+                          : per_warp ? blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)
+                                     : blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = per_block ? gridDim.x
+                           : per_warp ? (int64_t)gridDim.x * (blockDim.x >> 5)
+                                      : (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = first; u < total; u += stride) {
         const int pi = batch_find(w.off, w.np, u);
         const ProbDesc& P = w.desc[w.probs[pi]];
         const int64_t x = u - w.off[pi];
         const int n = P.n;
+        const int l = work_level(w, P);
         if constexpr (OP == B_WHITEN) {
             whiten_cta_step<T>(whiten_args_of(P), x, reinterpret_cast<double*>(smem_raw));
         } else if constexpr (OP == B_LEVEL) {
@@ -490,23 +773,25 @@ __global__ void __launch_bounds__(256) batch_generic_k(const BatchWork* wk) {
                           reinterpret_cast<T*>(P.R), P.cn2, P.cd2, P.bad);
             __syncthreads();
         } else if constexpr (OP == B_BACKSUB) {
-            backsub_row_generic<T>(n, P.k, l, x, reinterpret_cast<const T*>(P.R), nullptr, P.u);
+            backsub_warp<T, T, double>(n, P.k, l, x, reinterpret_cast<const T*>(P.R), (const T*)nullptr, P.u);
         } else if constexpr (OP == B_SELINV) {
             selinv_cta_row<T, SelAos<T>>(n, P.k, l, x, reinterpret_cast<const T*>(P.R),
                                          reinterpret_cast<T*>(P.Sx), P.cov, P.bad,
                                          reinterpret_cast<T*>(smem_raw));
         } else if constexpr (OP == B_REFINE_Q) {
-            refine_q_generic(refine_args_of(P), x);
+            refine_q_warp<float>(refine_args_of(P), x, reinterpret_cast<float*>(P.q));
         } else if constexpr (OP == B_REFINE_G) {
-            refine_g_generic(refine_args_of(P), x);
+            refine_g_warp<float>(refine_args_of(P), x, reinterpret_cast<const float*>(P.q),
+                                 reinterpret_cast<float*>(P.g));
         } else if constexpr (OP == B_RT_SOLVE) {
-            rt_solve_generic<T>(n, P.k, l, x, reinterpret_cast<const T*>(P.R),
-                                reinterpret_cast<double*>(P.g), reinterpret_cast<double*>(P.w));
+            rt_solve_warp<float, float>(n, P.k, l, x, reinterpret_cast<const float*>(P.R),
+                                        reinterpret_cast<float*>(P.g), reinterpret_cast<float*>(P.w));
         } else if constexpr (OP == B_BACKSUB_W) {
-            backsub_row_generic<T>(n, P.k, l, x, reinterpret_cast<const T*>(P.R),
-                                   reinterpret_cast<const double*>(P.w), reinterpret_cast<double*>(P.d));
+            backsub_warp<float, float, float>(n, P.k, l, x, reinterpret_cast<const float*>(P.R),
+                                              reinterpret_cast<const float*>(P.w),
+                                              reinterpret_cast<float*>(P.d));
         } else if constexpr (OP == B_ADD) {
-            P.u[x] += reinterpret_cast<const double*>(P.d)[x];
+            P.u[x] += (double)reinterpret_cast<const float*>(P.d)[x];
         }
     }
 }

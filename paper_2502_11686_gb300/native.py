@@ -18,11 +18,15 @@ KS_OK, KS_ERR_ARG, KS_ERR_NOT_SPD, KS_ERR_SINGULAR, KS_ERR_OOM, KS_ERR_CUDA, KS_
 STATUS_NAMES = {0: "KS_OK", 1: "KS_ERR_ARG", 2: "KS_ERR_NOT_SPD", 3: "KS_ERR_SINGULAR",
                 4: "KS_ERR_OOM", 5: "KS_ERR_CUDA", 6: "KS_ERR_TIMEOUT", 7: "KS_ERR_NO_FACTOR"}
 KS_FP64, KS_FP32_REFINE = 0, 1
+KS_TI_F, KS_TI_H, KS_TI_K, KS_TI_G, KS_TI_C = 1, 2, 4, 8, 16
 
 # Every symbol include/ks.h declares.
 EXPORTS = ("ks_default_options", "ks_create", "ks_smooth", "ks_covariances", "ks_residual",
            "ks_release", "ks_sync", "ks_destroy", "ks_last_error", "ks_max_n", "ks_max_m",
-           "ks_profile_read", "ks_smooth_static", "ks_smooth_batch")
+           "ks_profile_read", "ks_smooth_static", "ks_smooth_batch", "ks_generate",
+           "ks_server_create", "ks_server_submit", "ks_server_submit_synthetic",
+           "ks_server_covariances", "ks_server_wait", "ks_server_result", "ks_server_release",
+           "ks_server_stats", "ks_server_destroy")
 PHASES = ("whiten", "level", "backsub", "refine", "selinv", "copy", "batch")
 
 
@@ -42,7 +46,27 @@ class ks_problem(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int64), ("n", ctypes.c_int), ("m", ctypes.c_void_p),
                 ("F", ctypes.c_void_p), ("H", ctypes.c_void_p), ("c", ctypes.c_void_p),
                 ("K", ctypes.c_void_p), ("G", ctypes.c_void_p), ("o", ctypes.c_void_p),
-                ("C", ctypes.c_void_p), ("u_out", ctypes.c_void_p), ("cov_out", ctypes.c_void_p)]
+                ("C", ctypes.c_void_p), ("u_out", ctypes.c_void_p), ("cov_out", ctypes.c_void_p),
+                ("time_invariant", ctypes.c_uint)]
+
+
+class ks_server_options(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_active", ctypes.c_int),
+                ("keep_factors", ctypes.c_int)]
+
+
+class ks_request_info(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("info", ctypes.c_int64),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("k", ctypes.c_int64), ("n", ctypes.c_int)]
+
+
+class ks_server_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("ticks", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
+                ("bytes_budget", ctypes.c_size_t)]
 
 
 class KsError(RuntimeError):
@@ -99,6 +123,26 @@ def load():
         lib.ks_smooth_batch.argtypes = [P, I, ctypes.POINTER(ks_problem), ctypes.POINTER(I),
                                         ctypes.POINTER(I64)]
         lib.ks_smooth_batch.restype = I
+        lib.ks_generate.argtypes = [P, I64, I, I, ctypes.c_uint64, ctypes.c_double, P, P, P, P, P, P]
+        lib.ks_generate.restype = I
+        lib.ks_server_create.argtypes = [P, ctypes.POINTER(ks_server_options), ctypes.POINTER(P)]
+        lib.ks_server_create.restype = I
+        lib.ks_server_submit.argtypes = [P, ctypes.POINTER(ks_problem), ctypes.POINTER(I64)]
+        lib.ks_server_submit.restype = I
+        lib.ks_server_submit_synthetic.argtypes = [P, I64, I, I, ctypes.c_uint64, I, ctypes.POINTER(I64)]
+        lib.ks_server_submit_synthetic.restype = I
+        lib.ks_server_covariances.argtypes = [P, I64, P, ctypes.POINTER(I64)]
+        lib.ks_server_covariances.restype = I
+        lib.ks_server_wait.argtypes = [P, I64, ctypes.c_double, ctypes.POINTER(ks_request_info)]
+        lib.ks_server_wait.restype = I
+        lib.ks_server_result.argtypes = [P, I64, P, P]
+        lib.ks_server_result.restype = I
+        lib.ks_server_release.argtypes = [P, I64]
+        lib.ks_server_release.restype = I
+        lib.ks_server_stats.argtypes = [P, ctypes.POINTER(ks_server_counters)]
+        lib.ks_server_stats.restype = I
+        lib.ks_server_destroy.argtypes = [P]
+        lib.ks_server_destroy.restype = I
         _lib = lib
         return lib
 
@@ -209,17 +253,92 @@ def ks_smooth_static(device, stream, k, n, m, F, H, c, K, G, o, C, u_out, cov_ou
     return st, info.value, buf.value.decode()
 
 
+def _problem_struct(p, keep):
+    m = p["m"]
+    keep.append(m)
+    return ks_problem(int(p["k"]), int(p["n"]), ptr(m), ptr(p.get("F")), ptr(p.get("H")),
+                      ptr(p.get("c")), ptr(p.get("K")), ptr(p.get("G")), ptr(p.get("o")),
+                      ptr(p.get("C")), ptr(p["u_out"]), ptr(p.get("cov_out")),
+                      int(p.get("time_invariant", 0)))
+
+
+def ks_generate(ctx, k, n, m, seed, f_scale, F, H, K, G, C, o):
+    st = load().ks_generate(ctx, int(k), int(n), int(m), int(seed), float(f_scale), ptr(F), ptr(H),
+                            ptr(K), ptr(G), ptr(C), ptr(o))
+    _check(ctx, st)
+
+
+def ks_server_create(ctx, mem_budget=0, max_active=0, keep_factors=False):
+    o = ks_server_options(int(mem_budget), int(max_active), 1 if keep_factors else 0)
+    srv = ctypes.c_void_p()
+    st = load().ks_server_create(ctx, ctypes.byref(o), ctypes.byref(srv))
+    if st != KS_OK:
+        raise KsError(st, ks_last_error(ctx))
+    return srv
+
+
+def ks_server_submit(srv, problem) -> int:
+    keep = []
+    s = _problem_struct(problem, keep)
+    rid = ctypes.c_int64(0)
+    st = load().ks_server_submit(srv, ctypes.byref(s), ctypes.byref(rid))
+    if st != KS_OK:
+        raise KsError(st, "ks_server_submit failed")
+    return rid.value
+
+
+def ks_server_submit_synthetic(srv, k, n, m, seed, want_cov=False) -> int:
+    rid = ctypes.c_int64(0)
+    st = load().ks_server_submit_synthetic(srv, int(k), int(n), int(m), int(seed),
+                                           1 if want_cov else 0, ctypes.byref(rid))
+    if st != KS_OK:
+        raise KsError(st, "ks_server_submit_synthetic failed")
+    return rid.value
+
+
+def ks_server_covariances(srv, rid, cov_out=None) -> int:
+    fid = ctypes.c_int64(0)
+    st = load().ks_server_covariances(srv, int(rid), ptr(cov_out), ctypes.byref(fid))
+    if st != KS_OK:
+        raise KsError(st, "ks_server_covariances failed")
+    return fid.value
+
+
+def ks_server_wait(srv, rid, timeout_ms=-1.0) -> dict:
+    info = ks_request_info()
+    st = load().ks_server_wait(srv, int(rid), float(timeout_ms), ctypes.byref(info))
+    return {"status": st, "done": bool(info.done), "request_status": info.status,
+            "info": info.info, "queue_ms": info.queue_ms, "latency_ms": info.latency_ms,
+            "k": info.k, "n": info.n}
+
+
+def ks_server_result(srv, rid, u_out=None, cov_out=None):
+    st = load().ks_server_result(srv, int(rid), ptr(u_out), ptr(cov_out))
+    if st != KS_OK:
+        raise KsError(st, "ks_server_result failed")
+
+
+def ks_server_release(srv, rid):
+    return load().ks_server_release(srv, int(rid))
+
+
+def ks_server_stats(srv) -> dict:
+    c = ks_server_counters()
+    load().ks_server_stats(srv, ctypes.byref(c))
+    return {f: getattr(c, f) for f, _ in ks_server_counters._fields_}
+
+
+def ks_server_destroy(srv):
+    return load().ks_server_destroy(srv)
+
+
 def ks_smooth_batch(ctx, problems, check=True):
     """problems: list of dicts with k, n, m and the arrays of ks_smooth plus u_out / cov_out.
     Returns (status, per-problem statuses, per-problem infos)."""
     arr = (ks_problem * len(problems))()
     keep = []
     for i, p in enumerate(problems):
-        m = p["m"]
-        keep.append(m)
-        arr[i] = ks_problem(int(p["k"]), int(p["n"]), ptr(m), ptr(p.get("F")), ptr(p.get("H")),
-                            ptr(p.get("c")), ptr(p.get("K")), ptr(p.get("G")), ptr(p.get("o")),
-                            ptr(p.get("C")), ptr(p["u_out"]), ptr(p.get("cov_out")))
+        arr[i] = _problem_struct(p, keep)
     st_arr = (ctypes.c_int * len(problems))()
     info_arr = (ctypes.c_int64 * len(problems))()
     st = load().ks_smooth_batch(ctx, len(problems), arr, st_arr, info_arr)
