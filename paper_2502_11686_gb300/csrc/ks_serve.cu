@@ -146,6 +146,7 @@ size_t plan_request(ks_server* S, Req* r, bool apply) {
             D.Sx = P(o_sx);
             r->cov_dev = (double*)P(o_cov);
             D.cov = r->cov_dev;
+            cudaMemsetAsync(D.bad, 0xFF, ST_NCODES * sizeof(unsigned long long), S->st);
         }
         return off;
     }

@@ -114,7 +114,7 @@ def test_admission_waits_for_memory():
     probs = [(inputs.random_problem(3000, 6, 6, seed=40 + i), False) for i in range(8)]
     with Smoother(device=0, precision="fp64") as sm:
         refs = [alone(sm, p, False)[0] for p, _ in probs]
-        srv = native.ks_server_create(sm.ctx, mem_budget=6 << 20)   # about two requests at a time
+        srv = native.ks_server_create(sm.ctx, mem_budget=14 << 20)   # each request needs about 6.5 MB: two at a time
         reqs = [request(p, False) for p, _ in probs]
         ids = [native.ks_server_submit(srv, r) for r in reqs]
         queued_seen = native.ks_server_stats(srv)["queued"]
