@@ -340,6 +340,113 @@ def batch_arm(args):
     return 0
 
 
+def serve_arm(args):
+    """The serving loop: Poisson arrivals of synthetic requests (inputs generated on the device at
+    admission), k log-uniform in [1e2, 1e5], n uniform over the served state sizes, m = n; 10 %
+    of the requests get a covariance follow-up on their kept factor.  Reports per offered rate the
+    completed throughput and the p50 / p99 latency from submission to completion."""
+    import torch
+
+    from paper_2502_11686_gb300 import native
+
+    torch.cuda.set_device(0)
+    o = native.ks_default_options()
+    o.precision = native.KS_FP64 if args.precision == "fp64" else native.KS_FP32_REFINE
+    ctx = native.ks_create(o)
+    ns = [int(x) for x in args.serve_n.split(",")]
+    rates = [float(x) for x in args.rates.split(",")]
+    results = []
+    rng = np.random.default_rng(2024)
+    seed = 0
+    for rate in rates:
+        srv = native.ks_server_create(ctx, keep_factors=True)
+        lat, qms, cov_lat, done_steps = [], [], [], 0
+        lock = threading.Lock()
+        pending = []
+        stop = threading.Event()
+
+        def waiter():
+            nonlocal done_steps
+            while not stop.is_set() or pending:
+                with lock:
+                    item = pending.pop(0) if pending else None
+                if item is None:
+                    time.sleep(0.0005)
+                    continue
+                rid, k, follow = item
+                info = native.ks_server_wait(srv, rid)
+                with lock:
+                    lat.append(info["latency_ms"])
+                    qms.append(info["queue_ms"])
+                    done_steps += k
+                if follow:
+                    fid = native.ks_server_covariances(srv, rid)
+                    finfo = native.ks_server_wait(srv, fid)
+                    with lock:
+                        cov_lat.append(finfo["latency_ms"])
+                    native.ks_server_release(srv, fid)
+                native.ks_server_release(srv, rid)
+
+        th = threading.Thread(target=waiter, daemon=True)
+        th.start()
+        t0 = time.perf_counter()
+        t_next = t0
+        submitted = 0
+        saturated = False
+        while True:
+            now = time.perf_counter()
+            if now - t0 >= args.duration:
+                break
+            if submitted % 8 == 0 and native.ks_server_stats(srv)["queued"] > args.max_queue:
+                saturated = True   # offered load above capacity: stop before the backlog grows
+                break
+            if now < t_next:
+                time.sleep(min(t_next - now, 0.001))
+                continue
+            k = int(round(np.exp(rng.uniform(np.log(1e2), np.log(1e5)))))
+            n = int(rng.choice(ns))
+            rid = native.ks_server_submit_synthetic(srv, k, n, n, seed, want_cov=False)
+            seed += 1
+            with lock:
+                pending.append((rid, k, rng.uniform() < 0.1))
+            submitted += 1
+            t_next += rng.exponential(1.0 / rate)
+        submit_window = time.perf_counter() - t0
+        stop.set()
+        th.join()
+        total = time.perf_counter() - t0
+        stats = native.ks_server_stats(srv)
+        native.ks_server_destroy(srv)
+        lat_a = np.array(lat)
+        results.append({
+            "offered_req_per_s": rate, "saturated": saturated, "submitted": submitted,
+            "completed": len(lat),
+            "submit_window_s": submit_window, "drain_s": total - submit_window,
+            "throughput_steps_per_s": done_steps / total,
+            "throughput_req_per_s": len(lat) / total,
+            "p50_ms": float(np.percentile(lat_a, 50)) if len(lat_a) else None,
+            "p99_ms": float(np.percentile(lat_a, 99)) if len(lat_a) else None,
+            "p50_queue_ms": float(np.percentile(qms, 50)) if qms else None,
+            "cov_followups": len(cov_lat),
+            "p99_cov_ms": float(np.percentile(cov_lat, 99)) if cov_lat else None,
+            "ticks": stats["ticks"], "launches": stats["launches"]})
+        print(json.dumps({"serve_rate": results[-1]}), flush=True)
+        if saturated:
+            break
+    native.ks_destroy(ctx)
+    best = max(results, key=lambda r: r["throughput_steps_per_s"])
+    line = {"metric": METRIC, "value": best["throughput_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": len(rates), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (generated on the device at admission)",
+            "config": {"workload": "serve: Poisson arrivals, k log-uniform [1e2, 1e5], n in "
+                                   f"{ns}, m = n, 10 % covariance follow-ups",
+                       "precision": args.precision, "duration_s_per_rate": args.duration},
+            "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "rates": results}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,8 +454,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="long_k1e6_n6",
-                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + ["serve"])
     ap.add_argument("--nprob", type=int, default=None, help="batched workloads: problem count")
+    ap.add_argument("--rates", default="25,50,100,200,400,800,2000",
+                    help="serve workload: offered request rates (req/s) to sweep")
+    ap.add_argument("--duration", type=float, default=6.0, help="serve workload: seconds per rate")
+    ap.add_argument("--serve-n", default="6,24,48,128", help="serve workload: state sizes")
+    ap.add_argument("--max-queue", type=int, default=32,
+                    help="serve workload: a rate whose admission queue exceeds this is saturated")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_refine"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -357,6 +470,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "serve":
+        if args.impl == "reference":
+            return 0
+        if args.precision == "fp64" and "--precision" not in sys.argv:
+            args.precision = "fp32_refine"
+        return serve_arm(args)
     if args.workload in BATCH_WORKLOADS:
         if args.impl == "reference":
             return 0

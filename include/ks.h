@@ -287,7 +287,9 @@ ks_status ks_smooth_static(int device, void *stream, int64_t k, int n, int m,
                            double *u_out, double *cov_out, int64_t *info,
                            char *err, size_t err_len);
 
-/* Largest state dimension n this ctx's precision supports on its device. */
+/* Largest state dimension n this ctx's precision supports on its device (128 on GB300: up to
+ * 48 (FP64) / 64 (FP32) with shared-memory tiles, above that with the large-state kernels, which
+ * work on the records in device memory and require every m_i <= n). */
 int ks_max_n(const ks_ctx *ctx);
 
 /* Largest per-step observation count m_i supported for state dimension n. */

@@ -30,6 +30,8 @@ def nvcc() -> str:
 
 SMALL_UNIT = "ks_small_n.cu"   # compiled once per state dimension N = 1..SMALL_NMAX
 SMALL_NMAX = 8
+MED_UNIT = "ks_med_n.cu"       # compiled once per N in MED_NS
+MED_NS = (12, 16, 24, 32, 48, 64)
 
 
 def sources():
@@ -44,14 +46,28 @@ def units():
         if os.path.basename(src) == SMALL_UNIT:
             for n in range(1, SMALL_NMAX + 1):
                 out.append((src, f"{base}{n}.o", [f"-DKS_SMALL_N={n}"]))
+        elif os.path.basename(src) == MED_UNIT:
+            for n in MED_NS:
+                out.append((src, f"{base}{n}.o", [f"-DKS_MED_N={n}"]))
         else:
             out.append((src, base + ".o", []))
     return out
 
 
+def _headers_digest() -> str:
+    h = hashlib.sha256()
+    files = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
+    files.append(os.path.join(INCLUDE, "ks.h"))
+    for f in files:
+        h.update(f.encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def _digest() -> str:
     h = hashlib.sha256()
-    files = sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh"))
+    files = sources() + sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
     files.append(os.path.join(INCLUDE, "ks.h"))
     for f in files:
         h.update(f.encode())
@@ -71,15 +87,25 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     cc = nvcc()
     objs = []
 
+    hdr = _headers_digest()
+
     def compile_one(unit):
         src, oname, defs = unit
         obj = os.path.join(BUILD_DIR, oname)
         cmd = [cc, *NVCC_FLAGS, *defs, *extra_flags, "-c", src, "-o", obj]
+        h = hashlib.sha256(hdr.encode() + " ".join(cmd).encode())
+        with open(src, "rb") as fh:
+            h.update(fh.read())
+        ustamp = obj + ".stamp"
+        if not force and os.path.exists(obj) and os.path.exists(ustamp) and open(ustamp).read() == h.hexdigest():
+            return obj   # this unit and every header unchanged
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
         if verbose and (r.stdout or r.stderr):
             print(r.stdout + r.stderr)
+        with open(ustamp, "w") as fh:
+            fh.write(h.hexdigest())
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:

@@ -2,6 +2,8 @@
 // of host arrays, and the launch sequence of one smoothing call:
 //   whitening -> level 0 .. L-1 of the odd-even factorization -> base -> back substitution
 //   (levels L .. 0) [-> FP64 refinement in KS_FP32_REFINE mode] -> copy-out -> status.
+#include <cstdlib>
+
 #include "ks_host.h"
 
 using namespace ks;
@@ -14,6 +16,22 @@ const SmallOps* small_ops(int n) {
                                                     &small_ops_3, &small_ops_4, &small_ops_5,
                                                     &small_ops_6, &small_ops_7, &small_ops_8};
     return (n >= 1 && n <= SMALL_NMAX) ? table[n] : nullptr;
+}
+
+extern const MedOps med_ops_12, med_ops_16, med_ops_24, med_ops_32, med_ops_48, med_ops_64;
+const MedOps* med_ops(int n, bool fp32) {
+    if (const char* v = getenv("KS_NO_MED")) { if (*v && *v != '0') return nullptr; }
+    const MedOps* m = nullptr;
+    switch (n) {
+        case 12: m = &med_ops_12; break;
+        case 16: m = &med_ops_16; break;
+        case 24: m = &med_ops_24; break;
+        case 32: m = &med_ops_32; break;
+        case 48: m = &med_ops_48; break;
+        case 64: m = &med_ops_64; break;
+        default: return nullptr;
+    }
+    return (fp32 || m->fp64) ? m : nullptr;
 }
 }  // namespace ks
 
@@ -240,6 +258,7 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     wa.cn2 = (double*)(ws + o_cn2);
     wa.cd2 = (double*)(ws + o_cd2);
     wa.bad = ctx->d_bad;
+    wa.scratch = ws + o_lvlB;
     KS_CUDA(ctx, cudaMemsetAsync(resid, 0, (size_t)k * sizeof(double), st));
     {
         Phase ph(ctx, KS_PHASE_WHITEN);
@@ -255,6 +274,8 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
         while (nc > 1) {
             if (sops)
                 KS_CUDA(ctx, sops->level(nc, level, k, bufs[cur], bufs[cur ^ 1], R, resid, wa.cn2, wa.cd2, ctx->d_bad, fp32, st));
+            else if (const MedOps* mops = med_ops(n, fp32))
+                KS_CUDA(ctx, mops->level(nc, level, k, bufs[cur], bufs[cur ^ 1], R, resid, wa.cn2, wa.cd2, ctx->d_bad, fp32, st));
             else
                 KS_CUDA(ctx, launch_level(n, nc, level, k, bufs[cur], bufs[cur ^ 1], R, resid, wa.cn2, wa.cd2, ctx->d_bad, fp32, st));
             nc /= 2;

@@ -385,7 +385,8 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
 
     // ---- the first batch of a shape runs eagerly; groups seen for the first time are tuned
     //      there by timing candidate grids of their level-0 launch (it only reads the whitened
-    //      level 0 and rewrites its outputs, so it can be repeated) ----
+    //      level 0 and rewrites its outputs, so it can be repeated -- except the large-state
+    //      kernel, which works in place and keeps a fixed grid) ----
     bool tuning = false;
     for (const Group& g : groups)
         if (!ctx->tuned.count(g.sig(fp32)) && g.L >= 1) tuning = true;
@@ -413,7 +414,10 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
             const Launch& l = launches[i];
             const Group& g = groups[l.group];
             const std::string sig = g.sig(fp32);
-            if (l.op == B_LEVEL && l.level == 0 && !ctx->tuned.count(sig)) {
+            if (l.op == B_LEVEL && l.level == 0 && !ctx->tuned.count(sig) && !g.small &&
+                use_large(g.n, fp32)) {
+                ctx->tuned[sig] = 2;   // the large-state level kernel works in place: not repeatable
+            } else if (l.op == B_LEVEL && l.level == 0 && !ctx->tuned.count(sig)) {
                 static const int cand[] = {1, 2, 4, 8, 16, 32};
                 float best = 1e30f;
                 int best_bps = 8;

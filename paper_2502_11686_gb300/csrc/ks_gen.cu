@@ -61,33 +61,37 @@ __device__ double uniform(uint64_t seed, uint32_t tag, uint64_t idx) {
 
 enum { TAG_V = 1, TAG_LK = 2, TAG_DK = 3, TAG_LC = 4, TAG_DC = 5, TAG_G = 6, TAG_O = 7 };
 
-// One block builds the time-invariant matrices.
+// One block builds the time-invariant matrices.  Shared memory: the three reflection vectors
+// and the packed lower factor L of K or C (max(n, m)^2 / 2 doubles); F is formed in place in
+// device memory, one row per thread (each reflection only mixes the entries of a row).
 __global__ void gen_model_kernel(int n, int m, uint64_t seed, double f_scale, double* F, double* H,
                                  double* K, double* G, double* C) {
     extern __shared__ double sh[];
     double* V = sh;              // 3 x n reflection vectors
-    double* Q = sh + 3 * n;      // n x n
-    double* Lm = Q + n * n;      // max(n, m)^2 lower factor
+    double* Lp = sh + 3 * n;     // packed lower factor, row r at r (r + 1) / 2
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int e = tid; e < 3 * n; e += nth) V[e] = gauss(seed, TAG_V, e);
-    for (int e = tid; e < n * n; e += nth) Q[e] = (e / n == e % n) ? 1.0 : 0.0;
     __syncthreads();
-    // Q <- Q (I - 2 v v^T / |v|^2) for v = v1, v2, v3 (row by row).
+    double vv[3];
     for (int j = 0; j < 3; ++j) {
-        const double* v = V + j * n;
-        double vv = 0.0;
-        for (int p = 0; p < n; ++p) vv = fma(v[p], v[p], vv);
-        for (int r = tid; r < n; r += nth) {
-            double s = 0.0;
-            for (int p = 0; p < n; ++p) s = fma(Q[r * n + p], v[p], s);
-            s *= 2.0 / vv;
-            for (int p = 0; p < n; ++p) Q[r * n + p] = fma(-s, v[p], Q[r * n + p]);
-        }
-        __syncthreads();
+        vv[j] = 0.0;
+        for (int p = 0; p < n; ++p) vv[j] = fma(V[j * n + p], V[j * n + p], vv[j]);
     }
-    for (int e = tid; e < n * n; e += nth) {
-        F[e] = f_scale * Q[e];
-        H[e] = (e / n == e % n) ? 1.0 : 0.0;
+    // F <- I (I - 2 v1 v1^T / |v1|^2)(I - 2 v2 v2^T / |v2|^2)(I - 2 v3 v3^T / |v3|^2), row by row.
+    for (int r = tid; r < n; r += nth) {
+        double* Fr = F + (int64_t)r * n;
+        for (int p = 0; p < n; ++p) Fr[p] = (p == r) ? 1.0 : 0.0;
+        for (int j = 0; j < 3; ++j) {
+            const double* v = V + j * n;
+            double s = 0.0;
+            for (int p = 0; p < n; ++p) s = fma(Fr[p], v[p], s);
+            s *= 2.0 / vv[j];
+            for (int p = 0; p < n; ++p) Fr[p] = fma(-s, v[p], Fr[p]);
+        }
+        for (int p = 0; p < n; ++p) {
+            Fr[p] *= f_scale;
+            H[(int64_t)r * n + p] = (p == r) ? 1.0 : 0.0;
+        }
     }
     // K = L L^T and C = L L^T.
     for (int which = 0; which < 2; ++which) {
@@ -98,13 +102,15 @@ __global__ void gen_model_kernel(int n, int m, uint64_t seed, double f_scale, do
         __syncthreads();
         for (int e = tid; e < d * d; e += nth) {
             const int r = e / d, c = e % d;
-            Lm[e] = c < r ? 0.1 * gauss(seed, tl, e) : (c == r ? 0.5 + uniform(seed, td, r) : 0.0);
+            if (c <= r) Lp[r * (r + 1) / 2 + c] = c < r ? 0.1 * gauss(seed, tl, e) : 0.5 + uniform(seed, td, r);
         }
         __syncthreads();
         for (int e = tid; e < d * d; e += nth) {
             const int r = e / d, c = e % d;
+            const double* Lr = Lp + r * (r + 1) / 2;
+            const double* Lc = Lp + c * (c + 1) / 2;
             double s = 0.0;
-            for (int p = 0; p <= (r < c ? r : c); ++p) s = fma(Lm[r * d + p], Lm[c * d + p], s);
+            for (int p = 0; p <= (r < c ? r : c); ++p) s = fma(Lr[p], Lc[p], s);
             out[e] = s;
         }
     }
@@ -122,7 +128,8 @@ cudaError_t launch_generate(int64_t k, int n, int m, uint64_t seed, double f_sca
                             double* H, double* K, double* G, double* C, double* o,
                             cudaStream_t st) {
     const int d = n > m ? n : m;
-    const size_t smem = sizeof(double) * (size_t)(3 * n + n * n + d * d);
+    const size_t smem = sizeof(double) * (size_t)(3 * n + d * (d + 1) / 2);
+    if (smem > (size_t)SMEM_OPTIN_SM103) return cudaErrorInvalidValue;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(gen_model_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     gen_model_kernel<<<1, 256, smem, st>>>(n, m, seed, f_scale, F, H, K, G, C);

@@ -59,7 +59,7 @@ struct ks_ctx {
 
 namespace kshost {
 
-constexpr int KS_NMAX_API = 64;
+constexpr int KS_NMAX_API = LARGE_NMAX;
 
 inline ks_status fail(ks_ctx* ctx, ks_status s, const char* fmt, ...) {
     if (ctx) {
@@ -123,6 +123,11 @@ inline int max_n_for(const ks_ctx* ctx) {
     const bool fp32 = ctx->precision == KS_FP32_REFINE;
     int best = 0;
     for (int n = 1; n <= KS_NMAX_API; ++n) {
+        if (use_large(n, fp32)) {   // one thread block per unit, records in place
+            if ((int)large_smem_bytes(n, fp32) > ctx->smem_optin) break;
+            best = n;
+            continue;
+        }
         if (3 * n + 2 > 256) break;
         if (tile_smem_bytes(n, fp32) > ctx->smem_optin) break;
         if (selinv_smem_bytes(n, fp32) > ctx->smem_optin) break;
@@ -133,11 +138,13 @@ inline int max_n_for(const ks_ctx* ctx) {
 }
 
 inline int max_m_for(const ks_ctx* ctx, int n) {
-    int best = -1;
+    if (use_large(n, ctx->precision == KS_FP32_REFINE)) return n;
+    int best = n;   // m <= n: the large-state whitening covers what the column-owner one cannot
+    if ((int)large_smem_bytes(n, ctx->precision == KS_FP32_REFINE) > ctx->smem_optin) best = -1;
     for (int m = 0; m <= KS_NMAX_API; ++m) {
         if (n + m > 256) break;
         if (whiten_smem_bytes(n, m) > ctx->smem_optin) break;
-        best = m;
+        if (m > best) best = m;
     }
     return best;
 }

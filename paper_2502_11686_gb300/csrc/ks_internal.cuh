@@ -28,6 +28,8 @@ __device__ __forceinline__ void flag_error(unsigned long long* bad, int code, lo
 }
 
 __host__ __device__ __forceinline__ int odd_ld(int x) { return x | 1; }
+// Trailing zero bits of x > 0: the level at which column x - 1 is eliminated.
+__device__ __forceinline__ int ctz64(int64_t x) { return __ffsll((long long)x) - 1; }
 __host__ __device__ __forceinline__ int64_t level_cs(int n) { return 3LL * n * n + 2LL * n; }
 __host__ __device__ __forceinline__ int64_t rstore_rs(int n) { return 3LL * n * n + n; }
 
@@ -206,6 +208,7 @@ struct WhitenArgs {
     double* cn2;                  // out [k][n]: |Chat_i col|^2 + |B_i col|^2 (state i)
     double* cd2;                  // out [k][n]: |D_{i-1} col|^2 (state i; row 0 = 0)
     unsigned long long* bad;
+    void* scratch;                // large-state path: the second level buffer (free while whitening)
 };
 
 // Numerical singularity test of a finished diagonal block of R: |R_ii| is compared with the
@@ -228,6 +231,28 @@ __device__ __forceinline__ bool diag_is_singular(T d, double colnorm2, int n) {
 
 cudaError_t launch_whiten(const WhitenArgs& a, bool fp32, cudaStream_t st);
 
+// Large-state path (one thread block per unit, in place; see ks_large.cu): used for state
+// dimensions the column-owner kernels cannot hold in shared memory, up to LARGE_NMAX, with
+// every m_i <= n.
+constexpr int LARGE_NMAX = 128;
+__host__ __device__ __forceinline__ bool use_large(int n, bool fp32) { return fp32 ? n > 64 : n > 48; }
+size_t large_smem_bytes(int n, bool fp32);
+// Whether the column-owner whitening of (n, mmax) fits the opt-in shared memory of sm_103a;
+// otherwise (mmax <= n) the large-state whitening runs.
+constexpr int SMEM_OPTIN_SM103 = 232448;
+inline bool generic_whiten_fits(int n, int mmax) {
+    return (size_t)whiten_layout(n, mmax).total * sizeof(double) <= (size_t)SMEM_OPTIN_SM103;
+}
+cudaError_t launch_whiten_large(const WhitenArgs& a, bool fp32, cudaStream_t st);
+cudaError_t launch_level_large(int n, int64_t nc, int level, void* in, void* out, void* R,
+                               double* resid, const double* cn2, const double* cd2,
+                               unsigned long long* bad, bool fp32, cudaStream_t st);
+cudaError_t launch_selinv_large(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
+                                unsigned long long* bad, bool fp32, cudaStream_t st);
+struct BatchWork;
+cudaError_t launch_batch_large(int op, int n, const BatchWork* wk, bool fp32, unsigned grid,
+                               cudaStream_t st);
+
 cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
                          void* R, double* resid, const double* cn2, const double* cd2,
                          unsigned long long* bad, bool fp32, cudaStream_t st);
@@ -242,11 +267,6 @@ cudaError_t launch_selinv_soa(int n, int64_t k, int level, const void* R, void* 
 
 cudaError_t launch_base(int n, int64_t k, int L, const void* in, void* R, const double* cn2,
                         const double* cd2, unsigned long long* bad, bool fp32, cudaStream_t st);
-
-// Back substitution at one level: u_c = Rd_c^{-1}(rhs_c - Rl_c u_{c-2^l} - Rr_c u_{c+2^l}).
-// rhs = y from the R store when w == nullptr, else w ([k][n] FP64).
-cudaError_t launch_backsub(int n, int64_t k, int level, const void* R, const double* w,
-                           double* u, bool fp32, cudaStream_t st);
 
 // Odd-even SelInv at one level (Algorithm 2 body for every column eliminated at `level`).
 cudaError_t launch_selinv(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
@@ -272,10 +292,6 @@ struct RefineArgs {
     double* g;     // out [k][n]
     double* q;     // scratch [k-1][n]: K_i^{-1} (F_i u_i + c_i - H_i u_{i+1})
 };
-cudaError_t launch_refine_gradient(const RefineArgs& a, cudaStream_t st);
-cudaError_t launch_rt_solve(int n, int64_t k, int level, const void* R, double* g, double* w,
-                            bool fp32, cudaStream_t st);
-cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t st);
 
 // Warp-per-unit back substitution and mixed-precision refinement of the column-owner path.
 cudaError_t launch_backsub_warp(int n, int64_t k, int level, const void* R, bool fp32,
@@ -339,6 +355,7 @@ __device__ __forceinline__ WhitenArgs whiten_args_of(const ProbDesc& P) {
     a.F = P.F; a.H = P.H; a.c = P.c; a.K = P.K; a.G = P.G; a.o = P.o; a.C = P.C;
     a.level0 = P.lvl[0]; a.resid = P.resid + P.k; a.LK = P.LK; a.LC = P.LC;
     a.cn2 = P.cn2; a.cd2 = P.cd2; a.bad = P.bad;
+    a.scratch = P.lvl[1];
     return a;
 }
 
@@ -378,6 +395,18 @@ struct SmallOps {
     // Batched form: one launch of operation `op` over the work list at `wk` (device memory).
     cudaError_t (*batch)(int op, const BatchWork* wk, bool fp32, unsigned grid, cudaStream_t);
 };
+
+// Register-column level kernel of medium state dimensions (compiled for a few n); used in place
+// of the column-owner level kernel when med_ops(n, fp32) is not null.
+struct MedOps {
+    int n;
+    bool fp64;
+    cudaError_t (*level)(int64_t nc, int level, int64_t k, const void* in, void* out, void* R,
+                         double* resid, const double* cn2, const double* cd2,
+                         unsigned long long* bad, bool fp32, cudaStream_t);
+    cudaError_t (*batch_level)(const BatchWork* wk, bool fp32, unsigned grid, cudaStream_t);
+};
+const MedOps* med_ops(int n, bool fp32);
 
 // Batched column-owner launches (classes with n > 8 or some m_i > n).
 cudaError_t launch_batch_generic(int op, int n, int mmax, const BatchWork* wk, bool fp32,

@@ -1,0 +1,879 @@
+// ks_large.cu -- the large-state path (state dimension above the shared-memory limit of the
+// column-owner kernels, up to LARGE_NMAX = 128): whitening, the levels of the odd-even
+// factorization and SelInv with one thread block (256 threads) per unit, working IN PLACE on the
+// records in device memory (the unit's records stay in L2 while it is processed).
+//
+// * Levels (Section 3, steps 1-3 and the tail triple).  Every step is one "triangle over full
+//   block" Householder QR, done blocked: a panel of PB = 32 reflectors is factored in shared
+//   memory, its compact-WY form I - V T V^T built (T upper triangular, Schreiber & Van Loan
+//   1989), and the trailing columns -- the rest of the factor and the companion blocks -- are
+//   updated 32 columns at a time, X <- X - V (T^T (V^T X)).  The operands are the records
+//   themselves: the R store row of the eliminated column receives [Rd | Rl | Rr | y] directly,
+//   the new column's record is built in the output buffer, and the input records of the tile
+//   (each read by this tile only) serve as the full blocks.
+// * Whitening (Section 2): the Cholesky factors of K_i and C_i in FP64 (packed, shared memory,
+//   right-looking, all threads on the trailing triangle), the triangular solves in the working
+//   precision with one thread per right-hand column and 32 rows in registers, and the QR of the
+//   whitened observation block with the blocked routine above.  The free second level buffer
+//   holds the whitened observation block of each step.
+// * SelInv (Section 4, Algorithm 2) reorganised so that no buffer beyond the outputs is needed:
+//   with A = [Rl | Rr] and Ri = Rd^{-1} (shared memory),
+//     P = A S_II            -> the S store row of c          (S_II from the neighbours' S blocks)
+//     [Sl | Sr] = -Ri P     in place, row blocks top-down (Ri is upper triangular)
+//     M = Ri - [Sl | Sr] A^T -> the covariance slot of c
+//     S_cc = M Ri^T         in place, one row block at a time, then symmetrised,
+//   which is S_cc = Ri Ri^T - [Sl | Sr] T^T with T = Ri A, the form of Algorithm 2.
+#include "ks_internal.cuh"
+
+namespace ks {
+namespace large {
+
+constexpr int NTH = 256;   // threads per block
+constexpr int PB = 32;     // reflectors per panel
+constexpr int CW = 32;     // columns per trailing-update chunk
+constexpr int PMAX = LARGE_NMAX;
+constexpr int LDV = PB + 1;
+
+// Shared memory of the blocked QR (elements of T).
+struct QrSmem {
+    static constexpr int VB = 0;                       // PMAX x LDV: the panel's full-block part
+    static constexpr int TP = VB + PMAX * LDV;         // PB x LDV: the panel's triangle part
+    static constexpr int TM = TP + PB * LDV;           // PB x LDV: the T factor of the panel
+    static constexpr int YG = TM + PB * LDV;           // PB x LDV: V^T V
+    static constexpr int TAU = YG + PB * LDV;          // PB
+    static constexpr int XT = TAU + PB;                // PB x CW: chunk rows of the triangle part
+    static constexpr int XB = XT + PB * CW;            // PMAX x CW: chunk of the full block
+    static constexpr int W1 = XB + PMAX * CW;          // PB x CW
+    static constexpr int W2 = W1 + PB * CW;            // PB x CW
+    static constexpr int TOTAL = W2 + PB * CW;
+};
+
+// A column block of the stacked matrix [top ; bot]: top has the n rows of the triangle, bot the
+// p rows of the full block; element (r, c) at top[r * ldt + c] / bot[r * ldb + c].
+template <typename T>
+struct Blk {
+    T* top;
+    int64_t ldt;
+    T* bot;
+    int64_t ldb;
+    int ncols;
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reflector of panel column i (one warp): alpha = Tp[i][i], x = Vb[:, i] (p rows).  Scales the
+// full-block part to v (unit leading entry implied), sets Tp[i][i] = beta and tau[i].
+template <typename T>
+__device__ __forceinline__ void form_reflector(T* sm, int i, int p) {
+    T* Vb = sm + QrSmem::VB;
+    T* Tp = sm + QrSmem::TP;
+    const int lane = threadIdx.x & 31;
+    T s = T(0);
+    for (int r = lane; r < p; r += 32) s = fma(Vb[r * LDV + i], Vb[r * LDV + i], s);
+    const T sigma = warp_sum(s);
+    const T alpha = Tp[i * LDV + i];
+    const bool ok = sigma != T(0);
+    T g = T(0), tau = T(0), beta = alpha;
+    if (ok) {
+        const T nrm = sqrt(fma(alpha, alpha, sigma));
+        beta = alpha >= T(0) ? -nrm : nrm;
+        g = T(1) / (alpha - beta);
+        tau = (beta - alpha) / beta;
+    }
+    for (int r = lane; r < p; r += 32) Vb[r * LDV + i] *= g;
+    if (lane == 0) {
+        Tp[i * LDV + i] = beta;
+        sm[QrSmem::TAU + i] = tau;
+    }
+}
+
+// Trailing update of columns [c0, c0 + w) of block B by the panel's reflectors (top rows
+// kk0 .. kk0 + bw - 1): X <- X - V T^T V^T X.
+template <typename T>
+__device__ void apply_chunk(const Blk<T>& B, int c0, int w, int kk0, int bw, int p, T* sm) {
+    const T* Vb = sm + QrSmem::VB;
+    const T* Tm = sm + QrSmem::TM;
+    T* Xt = sm + QrSmem::XT;
+    T* Xb = sm + QrSmem::XB;
+    T* W1 = sm + QrSmem::W1;
+    T* W2 = sm + QrSmem::W2;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < PB * CW; e += NTH) {
+        const int i = e / CW, j = e - i * CW;
+        Xt[e] = (i < bw && j < w) ? B.top[(int64_t)(kk0 + i) * B.ldt + c0 + j] : T(0);
+    }
+    for (int e = tid; e < p * CW; e += NTH) {
+        const int r = e / CW, j = e - r * CW;
+        Xb[e] = j < w ? B.bot[(int64_t)r * B.ldb + c0 + j] : T(0);
+    }
+    __syncthreads();
+    const int q = tid >> 3, j0 = (tid & 7) * 4;   // 32 x 32 outputs, 4 per thread
+    {
+        T a0 = Xt[q * CW + j0], a1 = Xt[q * CW + j0 + 1], a2 = Xt[q * CW + j0 + 2], a3 = Xt[q * CW + j0 + 3];
+        for (int r = 0; r < p; ++r) {
+            const T v = Vb[r * LDV + q];
+            const T* x = Xb + r * CW + j0;
+            a0 = fma(v, x[0], a0);
+            a1 = fma(v, x[1], a1);
+            a2 = fma(v, x[2], a2);
+            a3 = fma(v, x[3], a3);
+        }
+        W1[q * CW + j0] = a0; W1[q * CW + j0 + 1] = a1; W1[q * CW + j0 + 2] = a2; W1[q * CW + j0 + 3] = a3;
+    }
+    __syncthreads();
+    {
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        for (int s = 0; s <= q; ++s) {
+            const T tv = Tm[s * LDV + q];
+            const T* x = W1 + s * CW + j0;
+            a0 = fma(tv, x[0], a0);
+            a1 = fma(tv, x[1], a1);
+            a2 = fma(tv, x[2], a2);
+            a3 = fma(tv, x[3], a3);
+        }
+        W2[q * CW + j0] = a0; W2[q * CW + j0 + 1] = a1; W2[q * CW + j0 + 2] = a2; W2[q * CW + j0 + 3] = a3;
+    }
+    __syncthreads();
+    for (int e = tid; e < bw * CW; e += NTH) {
+        const int i = e / CW, j = e - i * CW;
+        if (j < w) B.top[(int64_t)(kk0 + i) * B.ldt + c0 + j] = Xt[e] - W2[e];
+    }
+    for (int r = q; r < p; r += 32) {
+        T a0 = Xb[r * CW + j0], a1 = Xb[r * CW + j0 + 1], a2 = Xb[r * CW + j0 + 2], a3 = Xb[r * CW + j0 + 3];
+        for (int s = 0; s < bw; ++s) {
+            const T v = Vb[r * LDV + s];
+            const T* x = W2 + s * CW + j0;
+            a0 = fma(-v, x[0], a0);
+            a1 = fma(-v, x[1], a1);
+            a2 = fma(-v, x[2], a2);
+            a3 = fma(-v, x[3], a3);
+        }
+        T* dst = B.bot + (int64_t)r * B.ldb + c0 + j0;
+        if (j0 < w) dst[0] = a0;
+        if (j0 + 1 < w) dst[1] = a1;
+        if (j0 + 2 < w) dst[2] = a2;
+        if (j0 + 3 < w) dst[3] = a3;
+    }
+    __syncthreads();
+}
+
+// Blocked "triangle over full block" QR: F.top (n x n, upper triangular) over F.bot (p x n),
+// applied to the companion blocks C[0 .. nc).  On return F.top holds R; F.bot is consumed.
+template <typename T>
+__device__ void tpqrt_wy(int n, int p, const Blk<T>& F, const Blk<T>* C, int nc, T* sm) {
+    T* Vb = sm + QrSmem::VB;
+    T* Tp = sm + QrSmem::TP;
+    T* Tm = sm + QrSmem::TM;
+    T* Y = sm + QrSmem::YG;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (p == 0) return;
+    for (int kk0 = 0; kk0 < n; kk0 += PB) {
+        const int bw = n - kk0 < PB ? n - kk0 : PB;
+        __syncthreads();
+        for (int e = tid; e < p * PB; e += NTH) {
+            const int r = e / PB, j = e - r * PB;
+            Vb[r * LDV + j] = j < bw ? F.bot[(int64_t)r * F.ldb + kk0 + j] : T(0);
+        }
+        for (int e = tid; e < PB * PB; e += NTH) {
+            const int i = e / PB, j = e - i * PB;
+            Tp[i * LDV + j] = (i < bw && j < bw && i <= j) ? F.top[(int64_t)(kk0 + i) * F.ldt + kk0 + j] : T(0);
+        }
+        __syncthreads();
+        if (warp == 0) form_reflector<T>(sm, 0, p);
+        // Panel: reflector i applied to panel columns > i (column jj belongs to warp jj % 8);
+        // the owner of column i + 1 forms the next reflector right after updating it.
+        for (int i = 0; i < bw; ++i) {
+            __syncthreads();
+            const T tau = sm[QrSmem::TAU + i];
+            for (int jj = i + 1 + ((warp - (i + 1)) & 7); jj < bw; jj += 8) {
+                T s = T(0);
+                for (int r = lane; r < p; r += 32) s = fma(Vb[r * LDV + i], Vb[r * LDV + jj], s);
+                const T dot = warp_sum(s) + Tp[i * LDV + jj];
+                const T sc = tau * dot;
+                for (int r = lane; r < p; r += 32) Vb[r * LDV + jj] = fma(-sc, Vb[r * LDV + i], Vb[r * LDV + jj]);
+                __syncwarp();
+                if (lane == 0) Tp[i * LDV + jj] -= sc;
+                __syncwarp();
+                if (jj == i + 1) form_reflector<T>(sm, jj, p);
+            }
+        }
+        __syncthreads();
+        // R entries of the panel back to the triangle; Gram matrix V^T V of the panel.
+        for (int e = tid; e < bw * bw; e += NTH) {
+            const int i = e / bw, j = e - i * bw;
+            if (i <= j) F.top[(int64_t)(kk0 + i) * F.ldt + kk0 + j] = Tp[i * LDV + j];
+        }
+        for (int e = tid; e < PB * PB; e += NTH) {
+            const int a = e / PB, b = e - a * PB;
+            T s = T(0);
+            if (a < b && b < bw)
+                for (int r = 0; r < p; ++r) s = fma(Vb[r * LDV + a], Vb[r * LDV + b], s);
+            Y[a * LDV + b] = s;
+        }
+        __syncthreads();
+        // T factor (one warp; lane q keeps row q):  T[i][i] = tau_i,
+        // T[0:i, i] = -tau_i T[0:i, 0:i] (V^T v_i).
+        if (warp == 0) {
+            T row[PB];
+#pragma unroll
+            for (int i = 0; i < PB; ++i) {
+                T acc = T(0);
+#pragma unroll
+                for (int s = 0; s < PB; ++s)
+                    if (s < i && s >= lane) acc = fma(row[s], Y[s * LDV + i], acc);
+                const T ti = i < bw ? sm[QrSmem::TAU + i] : T(0);
+                row[i] = lane < i ? -ti * acc : (lane == i ? ti : T(0));
+            }
+#pragma unroll
+            for (int i = 0; i < PB; ++i) Tm[lane * LDV + i] = row[i];
+        }
+        __syncthreads();
+        // Trailing update: the rest of the factor, then every companion block.
+        for (int c0 = kk0 + bw; c0 < n; c0 += CW)
+            apply_chunk<T>(F, c0, (n - c0) < CW ? (n - c0) : CW, kk0, bw, p, sm);
+        for (int b = 0; b < nc; ++b)
+            for (int c0 = 0; c0 < C[b].ncols; c0 += CW)
+                apply_chunk<T>(C[b], c0, (C[b].ncols - c0) < CW ? (C[b].ncols - c0) : CW, kk0, bw, p, sm);
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// Level tile t (records in the generic layout; see the file comment).
+template <typename T>
+__device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* out, T* R,
+                           double* resid, const double* cn2, const double* cd2,
+                           unsigned long long* bad, T* sm) {
+    const int tid = threadIdx.x;
+    const int64_t nn = (int64_t)n * n;
+    const int64_t CS = level_cs(n), RS = rstore_rs(n);
+    const int64_t nt = nc / 2;
+    const int64_t j = 2 * t, s = j + 1;
+    const bool triple = (nc & 1) && (t == nt - 1);
+    const int64_t oj = ((j + 1) << level) - 1;
+    T* rj = in + j * CS;
+    T* rs = in + s * CS;
+    T* ro = out + t * CS;
+    T* Rj = R + oj * RS;
+    auto rec_C = [&](T* r) { return r; };
+    auto rec_RC = [&](T* r) { return r + nn; };
+    auto rec_E = [&](T* r) { return r + nn + n; };
+    auto rec_RE = [&](T* r) { return r + 3 * nn + n; };
+
+    // R row of column j: [Rd | Rl | Rr | y] <- [Chat_j | 0 | 0 | rC_j]
+    for (int64_t e = tid; e < nn; e += NTH) {
+        Rj[e] = rec_C(rj)[e];
+        Rj[nn + e] = T(0);
+        Rj[2 * nn + e] = T(0);
+    }
+    for (int r = tid; r < n; r += NTH) Rj[3 * nn + r] = rec_RC(rj)[r];
+    __syncthreads();
+    // step 1: [Chat_j ; -B_s], companions [0 ; D_s] (-> X_j, Dtilde_s) and [rC_j ; rE_s]
+    {
+        const Blk<T> F{Rj, n, rec_E(rs), 2 * n, n};
+        const Blk<T> C[2] = {{Rj + 2 * nn, n, rec_E(rs) + n, 2 * n, n}, {Rj + 3 * nn, 1, rec_RE(rs), 1, 1}};
+        tpqrt_wy<T>(n, n, F, C, 2, sm);
+    }
+    if (j >= 1) {
+        // step 2: [Rtilde_j ; D_j], companions [0 ; -B_j] (left), [X_j ; 0] (right), [t_j ; rE_j];
+        // the bottoms become the new column's coupling record.
+        for (int64_t e = tid; e < nn; e += NTH) {
+            const int64_t r = e / n, c = e - r * n;
+            rec_E(ro)[r * 2 * n + c] = rec_E(rj)[r * 2 * n + c];
+            rec_E(ro)[r * 2 * n + n + c] = T(0);
+        }
+        for (int r = tid; r < n; r += NTH) rec_RE(ro)[r] = rec_RE(rj)[r];
+        __syncthreads();
+        const Blk<T> F{Rj, n, rec_E(rj) + n, 2 * n, n};
+        const Blk<T> C[3] = {{Rj + nn, n, rec_E(ro), 2 * n, n},
+                             {Rj + 2 * nn, n, rec_E(ro) + n, 2 * n, n},
+                             {Rj + 3 * nn, 1, rec_RE(ro), 1, 1}};
+        tpqrt_wy<T>(n, n, F, C, 3, sm);
+    }
+    for (int c = tid; c < n; c += NTH)
+        if (diag_is_singular<T>(Rj[(int64_t)c * n + c], cn2[oj * n + c] + cd2[oj * n + c], n))
+            flag_error(bad, ST_SINGULAR, oj);
+    // new column t: [Chat'_t | rC'_t] starts as [Chat_s | rC_s]
+    for (int64_t e = tid; e < nn; e += NTH) rec_C(ro)[e] = rec_C(rs)[e];
+    for (int r = tid; r < n; r += NTH) rec_RC(ro)[r] = rec_RC(rs)[r];
+    T* re = nullptr;
+    if (triple) {
+        // tail column e: step 2 of [Chat_e ; D_e] with companions [0 ; -B_e] (-> Z_e), [rC_e ; rE_e]
+        const int64_t e_ = j + 2;
+        const int64_t oe = ((e_ + 1) << level) - 1;
+        re = in + e_ * CS;
+        T* Re = R + oe * RS;
+        for (int64_t e = tid; e < nn; e += NTH) {
+            Re[e] = rec_C(re)[e];
+            Re[nn + e] = T(0);
+            Re[2 * nn + e] = T(0);
+        }
+        for (int r = tid; r < n; r += NTH) Re[3 * nn + r] = rec_RC(re)[r];
+        __syncthreads();
+        const Blk<T> F{Re, n, rec_E(re) + n, 2 * n, n};
+        const Blk<T> C[2] = {{Re + nn, n, rec_E(re), 2 * n, n}, {Re + 3 * nn, 1, rec_RE(re), 1, 1}};
+        tpqrt_wy<T>(n, n, F, C, 2, sm);
+        for (int c = tid; c < n; c += NTH)
+            if (diag_is_singular<T>(Re[(int64_t)c * n + c], cn2[oe * n + c] + cd2[oe * n + c], n))
+                flag_error(bad, ST_SINGULAR, oe);
+    }
+    __syncthreads();
+    // step 3: [Chat_s ; Dtilde_s] with rhs [rC_s ; s_s]; for the tail a second pass over
+    // [Chat'_s ; Z_e] with [rC'_s ; z_e] (same R and residual as the QR of the three blocks)
+    {
+        const Blk<T> F{rec_C(ro), n, rec_E(rs) + n, 2 * n, n};
+        const Blk<T> C[1] = {{rec_RC(ro), 1, rec_RE(rs), 1, 1}};
+        tpqrt_wy<T>(n, n, F, C, 1, sm);
+    }
+    if (triple) {
+        const Blk<T> F{rec_C(ro), n, rec_E(re), 2 * n, n};
+        const Blk<T> C[1] = {{rec_RC(ro), 1, rec_RE(re), 1, 1}};
+        tpqrt_wy<T>(n, n, F, C, 1, sm);
+    }
+    if (threadIdx.x < 32) {
+        double acc = 0.0;
+        for (int r = threadIdx.x; r < n; r += 32) {
+            const double v = (double)rec_RE(rs)[r];
+            acc = fma(v, v, acc);
+            if (triple) {
+                const double z = (double)rec_RE(re)[r];
+                acc = fma(z, z, acc);
+            }
+        }
+        acc = warp_sum(acc);
+        if (threadIdx.x == 0) resid[oj] = acc;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// Whitening of step i.
+__device__ __forceinline__ int tri_(int r) { return r * (r + 1) / 2; }
+
+// Lower Cholesky factor of the d x d matrix held packed (row-major lower) in L, FP64, all
+// threads.  A non-positive or non-finite pivot flags ST_NOT_SPD at `step` and is replaced by 1.
+__device__ void chol_packed(double* L, int d, unsigned long long* bad, int64_t step) {
+    const int tid = threadIdx.x;
+    for (int j = 0; j < d; ++j) {
+        double ajj = L[tri_(j) + j];
+        if (!(ajj > 0.0) || !isfinite(ajj)) {
+            if (tid == 0) flag_error(bad, ST_NOT_SPD, step);
+            ajj = 1.0;
+        }
+        const double dj = sqrt(ajj), inv = 1.0 / dj;
+        __syncthreads();
+        if (tid == 0) L[tri_(j) + j] = dj;
+        for (int r = j + 1 + tid; r < d; r += NTH) L[tri_(r) + j] *= inv;
+        __syncthreads();
+        const int t = d - j - 1;
+        const int cnt = t * (t + 1) / 2;
+        for (int e = tid; e < cnt; e += NTH) {
+            int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+            while (tri_(rr + 1) <= e) ++rr;
+            while (tri_(rr) > e) --rr;
+            const int cc = e - tri_(rr);
+            const int r = j + 1 + rr, c = j + 1 + cc;
+            L[tri_(r) + c] = fma(-L[tri_(r) + j], L[tri_(c) + j], L[tri_(r) + c]);
+        }
+        __syncthreads();
+    }
+}
+
+// X <- L^{-1} X for one column of X (row stride ldx), L packed lower (type T): 32 rows at a
+// time in registers.
+template <typename T>
+__device__ void trsm_column(const T* L, int d, T* X, int64_t ldx) {
+    for (int rb = 0; rb < d; rb += 32) {
+        T acc[32];
+#pragma unroll
+        for (int ii = 0; ii < 32; ++ii) acc[ii] = (rb + ii < d) ? X[(int64_t)(rb + ii) * ldx] : T(0);
+        for (int q = 0; q < rb; ++q) {
+            const T xq = X[(int64_t)q * ldx];
+#pragma unroll
+            for (int ii = 0; ii < 32; ++ii)
+                if (rb + ii < d) acc[ii] = fma(-L[tri_(rb + ii) + q], xq, acc[ii]);
+        }
+#pragma unroll
+        for (int ii = 0; ii < 32; ++ii) {
+            if (rb + ii < d) {
+                const T x = acc[ii] / L[tri_(rb + ii) + rb + ii];
+                acc[ii] = x;
+#pragma unroll
+                for (int i2 = ii + 1; i2 < 32; ++i2)
+                    if (rb + i2 < d) acc[i2] = fma(-L[tri_(rb + i2) + rb + ii], x, acc[i2]);
+            }
+        }
+#pragma unroll
+        for (int ii = 0; ii < 32; ++ii)
+            if (rb + ii < d) X[(int64_t)(rb + ii) * ldx] = acc[ii];
+    }
+}
+
+// The same solve for one contiguous column by a whole warp (lane l holds rows l + 32 s).
+template <typename T>
+__device__ void trsm_column_warp(const T* L, int d, T* X) {
+    const int lane = threadIdx.x & 31;
+    T r[PMAX / 32];
+#pragma unroll
+    for (int s = 0; s < PMAX / 32; ++s) r[s] = (lane + 32 * s < d) ? X[lane + 32 * s] : T(0);
+    for (int i = 0; i < d; ++i) {
+        T x = T(0);
+        if ((i & 31) == lane) {
+#pragma unroll
+            for (int s = 0; s < PMAX / 32; ++s)
+                if ((i >> 5) == s) x = r[s] / L[tri_(i) + i];
+        }
+        x = __shfl_sync(0xffffffffu, x, i & 31);
+#pragma unroll
+        for (int s = 0; s < PMAX / 32; ++s) {
+            const int ii = lane + 32 * s;
+            if (ii > i && ii < d) r[s] = fma(-L[tri_(ii) + i], x, r[s]);
+            if (ii == i) r[s] = x;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < PMAX / 32; ++s)
+        if (lane + 32 * s < d) X[lane + 32 * s] = r[s];
+}
+
+struct WhitenSmem {
+    // FP64 packed factor, then its working-precision copy; the QR's buffers overlay both.
+    static size_t bytes(int n, bool fp32) {
+        const size_t tri = (size_t)n * (n + 1) / 2;
+        size_t chol = tri * sizeof(double) + (fp32 ? tri * sizeof(float) : 0);
+        chol = (chol + 15) & ~(size_t)15;
+        const size_t qr = (size_t)QrSmem::TOTAL * (fp32 ? sizeof(float) : sizeof(double));
+        return chol > qr ? chol : qr;
+    }
+};
+
+template <typename T>
+__device__ void whiten_step(const WhitenArgs& a, int64_t i, unsigned char* smem) {
+    const int n = a.n, tid = threadIdx.x;
+    const int64_t nn = (int64_t)n * n, CS = level_cs(n);
+    double* Lpk = reinterpret_cast<double*>(smem);
+    const int tri = n * (n + 1) / 2;
+    T* LT = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(Lpk) : reinterpret_cast<T*>(Lpk + tri);
+    T* out = reinterpret_cast<T*>(a.level0);
+    T* rec = out + i * CS;
+    int mi;
+    int64_t go, co;
+    if (a.m_uniform >= 0) {
+        mi = a.m_uniform;
+        go = i * mi;
+        co = i * (int64_t)mi * mi;
+    } else {
+        mi = a.m[i];
+        go = a.goff[i];
+        co = a.coff[i];
+    }
+    const bool hasE = i + 1 < a.k;
+    for (int64_t e = tid; e < nn + n; e += NTH) rec[e] = T(0);   // [Chat_i | rC_i] <- 0
+    T* En = out + (i + 1) * CS + nn + n;                         // E_{i+1}: [-B_i | D_i] (n x 2n)
+    T* REn = En + 2 * nn;
+    if (hasE) {
+        const double* Ki = a.K + ti_step(a.ti, TI_K, i) * nn;
+        const double* Fi = a.F + ti_step(a.ti, TI_F, i) * nn;
+        const double* Hi = a.H + ti_step(a.ti, TI_H, i) * nn;
+        for (int64_t e = tid; e < nn; e += NTH) {
+            const int r = (int)(e / n), c = (int)(e - (int64_t)r * n);
+            if (c <= r) Lpk[tri_(r) + c] = Ki[e];
+            En[(int64_t)r * 2 * n + c] = (T)(-Fi[e]);
+            En[(int64_t)r * 2 * n + n + c] = (T)Hi[e];
+        }
+        for (int r = tid; r < n; r += NTH) REn[r] = a.c ? (T)a.c[i * n + r] : T(0);
+        __syncthreads();
+        chol_packed(Lpk, n, a.bad, i);
+        if (a.LK != nullptr) {
+            double* lk = a.LK + i * nn;
+            for (int64_t e = tid; e < nn; e += NTH) {
+                const int r = (int)(e / n), c = (int)(e - (int64_t)r * n);
+                lk[e] = c <= r ? Lpk[tri_(r) + c] : 0.0;
+            }
+        }
+        if (sizeof(T) != sizeof(double)) {
+            for (int e = tid; e < tri; e += NTH) LT[e] = (T)Lpk[e];
+            __syncthreads();
+        }
+        for (int col = tid; col < 2 * n; col += NTH) trsm_column<T>(LT, n, En + col, 2 * n);
+        if (2 * n < NTH) {
+            if (tid == 2 * n) trsm_column<T>(LT, n, REn, 1);
+        } else if (tid < 32) {
+            trsm_column_warp<T>(LT, n, REn);
+        }
+        __syncthreads();
+    }
+    T* Gm = reinterpret_cast<T*>(a.scratch) + i * (int64_t)n * (n + 1);   // mi x (n + 1)
+    if (mi > 0) {
+        const double* Ci = a.C + ((a.ti & TI_C) ? 0 : co);
+        const double* Gi = a.G + ((a.ti & TI_G) ? 0 : go) * n;
+        for (int e = tid; e < mi * mi; e += NTH) {
+            const int r = e / mi, c = e - r * mi;
+            if (c <= r) Lpk[tri_(r) + c] = Ci[e];
+        }
+        for (int64_t e = tid; e < (int64_t)mi * n; e += NTH) {
+            const int r = (int)(e / n), c = (int)(e - (int64_t)r * n);
+            Gm[(int64_t)r * (n + 1) + c] = (T)Gi[e];
+        }
+        for (int r = tid; r < mi; r += NTH) Gm[(int64_t)r * (n + 1) + n] = (T)a.o[go + r];
+        __syncthreads();
+        chol_packed(Lpk, mi, a.bad, i);
+        if (a.LC != nullptr) {
+            for (int e = tid; e < mi * mi; e += NTH) {
+                const int r = e / mi, c = e - r * mi;
+                a.LC[co + e] = c <= r ? Lpk[tri_(r) + c] : 0.0;
+            }
+        }
+        const int mtri = mi * (mi + 1) / 2;
+        if (sizeof(T) != sizeof(double)) {
+            T* LTm = reinterpret_cast<T*>(Lpk + mtri);
+            for (int e = tid; e < mtri; e += NTH) LTm[e] = (T)Lpk[e];
+            __syncthreads();
+            for (int col = tid; col <= n; col += NTH) trsm_column<T>(LTm, mi, Gm + col, n + 1);
+        } else {
+            for (int col = tid; col <= n; col += NTH)
+                trsm_column<T>(reinterpret_cast<T*>(Lpk), mi, Gm + col, n + 1);
+        }
+        __syncthreads();
+        // [Chat_i | rC_i] = R of [0 ; L_C^{-1} [G_i | o_i]]
+        const Blk<T> F{rec, n, Gm, n + 1, n};
+        const Blk<T> C[1] = {{rec + nn, 1, Gm + n, n + 1, 1}};
+        tpqrt_wy<T>(n, mi, F, C, 1, reinterpret_cast<T*>(smem));
+    }
+    if (tid < 32) {
+        double acc = 0.0;
+        for (int r = tid; r < mi; r += 32) {
+            const double v = (double)Gm[(int64_t)r * (n + 1) + n];
+            acc = fma(v, v, acc);
+        }
+        acc = warp_sum(acc);
+        if (tid == 0) a.resid[i] = acc;
+    }
+    for (int col = tid; col < n; col += NTH) {
+        double sc = 0.0, sb = 0.0, sd = 0.0;
+        for (int r = 0; r <= col; ++r) {
+            const double v = (double)rec[(int64_t)r * n + col];
+            sc = fma(v, v, sc);
+        }
+        if (hasE) {
+            for (int r = 0; r < n; ++r) {
+                const double b = (double)En[(int64_t)r * 2 * n + col];
+                const double d = (double)En[(int64_t)r * 2 * n + n + col];
+                sb = fma(b, b, sb);
+                sd = fma(d, d, sd);
+            }
+            a.cd2[(i + 1) * n + col] = sd;
+        }
+        a.cn2[i * n + col] = sc + sb;
+        if (i == 0) a.cd2[col] = 0.0;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+// SelInv: CTA GEMM over row blocks of 32 rows and column tiles of 128, 4 x 4 per thread.
+constexpr int GM = 32, GN = 128, GK = 16;
+
+struct SelSmem {
+    static size_t bytes(int n, bool fp32) {
+        return (size_t)(n * n + GK * GM + GK * GN) * (fp32 ? sizeof(float) : sizeof(double));
+    }
+};
+
+// C[i][j] (i < M, j < N) = sum_{q = klo(i0) .. K-1} A(i, q) B(q, j), stored by st(i, j, acc) after
+// all of the tile's reads; row blocks in ascending order.
+template <typename T, typename FA, typename FB, typename FK, typename FS>
+__device__ void gemm_rows(int M, int N, int K, FA A, FB B, FK klo, FS st, T* As, T* Bs) {
+    const int tid = threadIdx.x;
+    const int rg = tid >> 5, cg = tid & 31;
+    for (int i0 = 0; i0 < M; i0 += GM) {
+        for (int j0 = 0; j0 < N; j0 += GN) {
+            T acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+            for (int k0 = klo(i0); k0 < K; k0 += GK) {
+                __syncthreads();
+                for (int e = tid; e < GK * GM; e += NTH) {
+                    const int i = e / GK, kk = e - i * GK;
+                    As[kk * GM + i] = (i0 + i < M && k0 + kk < K) ? A(i0 + i, k0 + kk) : T(0);
+                }
+                for (int e = tid; e < GK * GN; e += NTH) {
+                    const int kk = e / GN, jj = e - kk * GN;
+                    Bs[kk * GN + jj] = (j0 + jj < N && k0 + kk < K) ? B(k0 + kk, j0 + jj) : T(0);
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < GK; ++kk) {
+                    T av[4], bv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) av[a] = As[kk * GM + rg * 4 + a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) bv[b] = Bs[kk * GN + cg * 4 + b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int i = i0 + rg * 4 + a, jx = j0 + cg * 4 + b;
+                    if (i < M && jx < N) st(i, jx, acc[a][b]);
+                }
+        }
+    }
+    __syncthreads();
+}
+
+// Row q of level `level`.  Sx row c = [Sl (n x n) | Sr (n x n)], Sd = covariances (FP64).
+template <typename T>
+__device__ void selinv_row(int n, int64_t k, int level, int64_t q, const T* __restrict__ R, T* Sx,
+                           double* Sd, unsigned long long* bad, T* sm) {
+    const int tid = threadIdx.x;
+    const int64_t nn = (int64_t)n * n;
+    const int64_t c = ((2 * q + 1) << level) - 1;
+    if (c >= k) return;
+    const int64_t a = c - (1LL << level), b = c + (1LL << level);
+    const bool ha = a >= 0, hb = b < k;
+    int sab_src = 0;   // 1: S_ab = Sr_a, 2: S_ab = Sl_b^T
+    if (ha && hb) sab_src = (ctz64(a + 1) == level + 1) ? 1 : 2;
+    const T* Rc = R + c * rstore_rs(n);
+    const T* Rd = Rc;
+    const T* Rl = Rc + nn;
+    const T* Rr = Rc + 2 * nn;
+    T* Sl = Sx + c * 2 * nn;
+    T* Sr = Sl + nn;
+    T* Ri = sm;
+    T* As = sm + nn;
+    T* Bs = As + GK * GM;
+    double* slot = Sd + c * nn;
+    // M and then S_cc share the FP64 covariance slot; in FP32 M sits in its second half so that
+    // writing row block I of S_cc (doubles) only overwrites rows of M already consumed.
+    T* Mx = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(slot) : reinterpret_cast<T*>(slot) + nn;
+
+    // Ri = Rd^{-1} (upper triangular), one thread per column.
+    for (int64_t e = tid; e < nn; e += NTH) Ri[e] = T(0);
+    __syncthreads();
+    for (int jc = tid; jc < n; jc += NTH) {
+        for (int i = jc; i >= 0; --i) {
+            T s = (i == jc) ? T(1) : T(0);
+            for (int p = i + 1; p <= jc; ++p) s = fma(-Rd[(int64_t)i * n + p], Ri[(int64_t)p * n + jc], s);
+            Ri[(int64_t)i * n + jc] = s / Rd[(int64_t)i * n + i];
+        }
+    }
+    __syncthreads();
+    auto Aop = [&](int i, int p) -> T {   // [Rl | Rr]
+        return p < n ? (ha ? Rl[(int64_t)i * n + p] : T(0)) : (hb ? Rr[(int64_t)i * n + p - n] : T(0));
+    };
+    auto Sab = [&](int r, int cc) -> T {  // S_{a,b}
+        if (sab_src == 1) return Sx[a * 2 * nn + nn + (int64_t)r * n + cc];
+        if (sab_src == 2) return Sx[b * 2 * nn + (int64_t)cc * n + r];
+        return T(0);
+    };
+    auto Sii = [&](int p, int qq) -> T {
+        if (p < n) {
+            if (qq < n) return ha ? (T)Sd[a * nn + (int64_t)p * n + qq] : T(0);
+            return Sab(p, qq - n);
+        }
+        if (qq < n) return Sab(qq, p - n);
+        return hb ? (T)Sd[b * nn + (int64_t)(p - n) * n + (qq - n)] : T(0);
+    };
+    auto k0 = [](int) { return 0; };
+    // P = A S_II -> [Sl | Sr]
+    gemm_rows<T>(n, 2 * n, 2 * n, Aop, Sii, k0,
+                 [&](int i, int j, T v) { if (j < n) Sl[(int64_t)i * n + j] = v; else Sr[(int64_t)i * n + j - n] = v; },
+                 As, Bs);
+    // [Sl | Sr] = -Ri P (in place; row block i0 reads rows >= i0 only)
+    auto Pop = [&](int p, int j) -> T { return j < n ? Sl[(int64_t)p * n + j] : Sr[(int64_t)p * n + j - n]; };
+    gemm_rows<T>(n, 2 * n, n, [&](int i, int p) -> T { return Ri[(int64_t)i * n + p]; }, Pop,
+                 [](int i0) { return (i0 / GK) * GK; },
+                 [&](int i, int j, T v) { if (j < n) Sl[(int64_t)i * n + j] = -v; else Sr[(int64_t)i * n + j - n] = -v; },
+                 As, Bs);
+    // M = Ri - [Sl | Sr] A^T
+    gemm_rows<T>(n, n, 2 * n, Pop, [&](int p, int j) -> T { return Aop(j, p); }, k0,
+                 [&](int i, int j, T v) { Mx[(int64_t)i * n + j] = Ri[(int64_t)i * n + j] - v; }, As, Bs);
+    // S_cc = M Ri^T, row block by row block in place (doubles)
+    gemm_rows<T>(n, n, n, [&](int i, int p) -> T { return Mx[(int64_t)i * n + p]; },
+                 [&](int p, int j) -> T { return Ri[(int64_t)j * n + p]; }, k0,
+                 [&](int i, int j, T v) { slot[(int64_t)i * n + j] = (double)v; }, As, Bs);
+    // symmetrise, check the diagonal
+    for (int64_t e = tid; e < nn; e += NTH) {
+        const int r = (int)(e / n), cc = (int)(e - (int64_t)r * n);
+        if (r < cc) {
+            const double v = 0.5 * (slot[(int64_t)r * n + cc] + slot[(int64_t)cc * n + r]);
+            slot[(int64_t)r * n + cc] = v;
+            slot[(int64_t)cc * n + r] = v;
+        } else if (r == cc) {
+            const T v = (T)slot[e];
+            if (!(v > T(0))) flag_error(bad, ST_SINGULAR, c);
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTH) whiten_k(WhitenArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int64_t i = blockIdx.x; i < a.k; i += gridDim.x) whiten_step<T>(a, i, smem_raw);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTH) level_k(int n, int64_t nc, int level, T* in, T* out, T* R,
+                                               double* resid, const double* cn2, const double* cd2,
+                                               unsigned long long* bad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int64_t t = blockIdx.x; t < nc / 2; t += gridDim.x)
+        level_tile<T>(n, nc, level, t, in, out, R, resid, cn2, cd2, bad, reinterpret_cast<T*>(smem_raw));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTH) selinv_k(int n, int64_t k, int level, const T* R, T* Sx,
+                                                double* Sd, unsigned long long* bad) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t rows = (k >> level) - (k >> (level + 1));
+    for (int64_t q = blockIdx.x; q < rows; q += gridDim.x)
+        selinv_row<T>(n, k, level, q, R, Sx, Sd, bad, reinterpret_cast<T*>(smem_raw));
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(NTH) batch_k(const BatchWork* wk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const BatchWork w = *wk;
+    const int64_t total = w.off[w.np];
+    for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
+        const int pi = batch_find(w.off, w.np, u);
+        const ProbDesc& P = w.desc[w.probs[pi]];
+        const int64_t x = u - w.off[pi];
+        const int l = work_level(w, P);
+        if constexpr (OP == B_WHITEN) {
+            whiten_step<T>(whiten_args_of(P), x, smem_raw);
+        } else if constexpr (OP == B_LEVEL) {
+            level_tile<T>(P.n, P.k >> l, l, x, reinterpret_cast<T*>(P.lvl[l & 1]),
+                          reinterpret_cast<T*>(P.lvl[(l + 1) & 1]), reinterpret_cast<T*>(P.R), P.resid,
+                          P.cn2, P.cd2, P.bad, reinterpret_cast<T*>(smem_raw));
+        } else {
+            selinv_row<T>(P.n, P.k, l, x, reinterpret_cast<const T*>(P.R), reinterpret_cast<T*>(P.Sx),
+                          P.cov, P.bad, reinterpret_cast<T*>(smem_raw));
+        }
+    }
+}
+
+unsigned grid_of(int64_t units, int per_sm) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int64_t g = (int64_t)sms * per_sm;
+    return (unsigned)(units < g ? (units < 1 ? 1 : units) : g);
+}
+
+template <typename K>
+void set_smem(K kern, size_t bytes) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+size_t qr_bytes(bool fp32) { return (size_t)QrSmem::TOTAL * (fp32 ? sizeof(float) : sizeof(double)); }
+
+}  // namespace large
+
+size_t large_smem_bytes(int n, bool fp32) {
+    using namespace large;
+    size_t m = WhitenSmem::bytes(n, fp32);
+    if (qr_bytes(fp32) > m) m = qr_bytes(fp32);
+    if (SelSmem::bytes(n, fp32) > m) m = SelSmem::bytes(n, fp32);
+    return m;
+}
+
+cudaError_t launch_whiten_large(const WhitenArgs& a, bool fp32, cudaStream_t st) {
+    using namespace large;
+    const size_t smem = WhitenSmem::bytes(a.n, fp32);
+    const unsigned grid = grid_of(a.k, 2);
+    if (fp32) {
+        set_smem(whiten_k<float>, smem);
+        whiten_k<float><<<grid, NTH, smem, st>>>(a);
+    } else {
+        set_smem(whiten_k<double>, smem);
+        whiten_k<double><<<grid, NTH, smem, st>>>(a);
+    }
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_large(int n, int64_t nc, int level, void* in, void* out, void* R,
+                               double* resid, const double* cn2, const double* cd2,
+                               unsigned long long* bad, bool fp32, cudaStream_t st) {
+    using namespace large;
+    if (nc < 2) return cudaSuccess;
+    const size_t smem = qr_bytes(fp32);
+    const unsigned grid = grid_of(nc / 2, 2);
+    if (fp32) {
+        set_smem(level_k<float>, smem);
+        level_k<float><<<grid, NTH, smem, st>>>(n, nc, level, (float*)in, (float*)out, (float*)R, resid, cn2, cd2, bad);
+    } else {
+        set_smem(level_k<double>, smem);
+        level_k<double><<<grid, NTH, smem, st>>>(n, nc, level, (double*)in, (double*)out, (double*)R, resid, cn2, cd2, bad);
+    }
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_selinv_large(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
+                                unsigned long long* bad, bool fp32, cudaStream_t st) {
+    using namespace large;
+    const int64_t rows = (k >> level) - (k >> (level + 1));
+    if (rows <= 0) return cudaSuccess;
+    const size_t smem = SelSmem::bytes(n, fp32);
+    const unsigned grid = grid_of(rows, fp32 ? 2 : 1);
+    if (fp32) {
+        set_smem(selinv_k<float>, smem);
+        selinv_k<float><<<grid, NTH, smem, st>>>(n, k, level, (const float*)R, (float*)Sx, Sd, bad);
+    } else {
+        set_smem(selinv_k<double>, smem);
+        selinv_k<double><<<grid, NTH, smem, st>>>(n, k, level, (const double*)R, (double*)Sx, Sd, bad);
+    }
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_large(int op, int n, const BatchWork* wk, bool fp32, unsigned grid,
+                               cudaStream_t st) {
+    using namespace large;
+    size_t smem = 0;
+    if (op == B_WHITEN) smem = WhitenSmem::bytes(n, fp32);
+    else if (op == B_LEVEL) smem = qr_bytes(fp32);
+    else if (op == B_SELINV) smem = SelSmem::bytes(n, fp32);
+    else return cudaErrorInvalidValue;
+#define KS_LARGE_BATCH(TT, OPV)                       \
+    do {                                              \
+        set_smem(batch_k<TT, OPV>, smem);             \
+        batch_k<TT, OPV><<<grid, NTH, smem, st>>>(wk); \
+    } while (0)
+    if (fp32) {
+        if (op == B_WHITEN) KS_LARGE_BATCH(float, B_WHITEN);
+        else if (op == B_LEVEL) KS_LARGE_BATCH(float, B_LEVEL);
+        else KS_LARGE_BATCH(float, B_SELINV);
+    } else {
+        if (op == B_WHITEN) KS_LARGE_BATCH(double, B_WHITEN);
+        else if (op == B_LEVEL) KS_LARGE_BATCH(double, B_LEVEL);
+        else KS_LARGE_BATCH(double, B_SELINV);
+    }
+#undef KS_LARGE_BATCH
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+}  // namespace ks

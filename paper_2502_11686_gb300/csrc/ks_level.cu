@@ -77,6 +77,8 @@ static cudaError_t launch_level_io(int n, int64_t nc, int level, int64_t k, cons
 cudaError_t launch_level(int n, int64_t nc, int level, int64_t k, const void* in, void* out,
                          void* R, double* resid, const double* cn2, const double* cd2,
                          unsigned long long* bad, bool fp32, cudaStream_t st) {
+    if (use_large(n, fp32))   // works in place: each input record is read by one tile only
+        return launch_level_large(n, nc, level, const_cast<void*>(in), out, R, resid, cn2, cd2, bad, fp32, st);
     return launch_level_io<AosIO>(n, nc, level, k, in, out, R, resid, cn2, cd2, bad, fp32, st);
 }
 

@@ -35,7 +35,6 @@ struct Dims {
 
 __host__ __device__ constexpr int tri(int N, int r, int c) { return r * N - r * (r - 1) / 2 + (c - r); }
 
-__device__ __forceinline__ int ctz64(int64_t x) { return __ffsll((long long)x) - 1; }
 
 // Level buffer view (two planes).
 template <typename T, int N>

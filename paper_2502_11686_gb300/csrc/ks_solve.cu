@@ -14,52 +14,9 @@
 #include <algorithm>
 
 #include "ks_generic.cuh"
+#include "ks_warp.cuh"
 
 namespace ks {
-
-constexpr int KS_NMAX = 64;
-
-__device__ __forceinline__ int ctz64(int64_t x) { return __ffsll((long long)x) - 1; }
-
-template <typename TR>
-__device__ void backsub_row_generic(int n, int64_t k, int level, int64_t q, const TR* __restrict__ R,
-                                    const double* __restrict__ w, double* __restrict__ u) {
-    const int64_t c = ((2 * q + 1) << level) - 1;
-    if (c >= k) return;
-    const int nn = n * n;
-    const TR* Rc = R + c * rstore_rs(n);
-    const int64_t a = c - (1LL << level), b = c + (1LL << level);
-    double r[KS_NMAX];
-    for (int i = 0; i < n; ++i) r[i] = w ? w[c * n + i] : (double)Rc[3 * nn + i];
-    if (a >= 0) {
-        const double* ua = u + a * n;
-        for (int i = 0; i < n; ++i) {
-            double s = r[i];
-            for (int p = 0; p < n; ++p) s = fma(-(double)Rc[nn + i * n + p], ua[p], s);
-            r[i] = s;
-        }
-    }
-    if (b < k) {
-        const double* ub = u + b * n;
-        for (int i = 0; i < n; ++i) {
-            double s = r[i];
-            for (int p = 0; p < n; ++p) s = fma(-(double)Rc[2 * nn + i * n + p], ub[p], s);
-            r[i] = s;
-        }
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        double s = r[i];
-        for (int p = i + 1; p < n; ++p) s = fma(-(double)Rc[i * n + p], r[p], s);
-        r[i] = s / (double)Rc[i * n + i];
-    }
-    for (int i = 0; i < n; ++i) u[c * n + i] = r[i];
-}
-
-template <typename TR>
-__global__ void backsub_kernel(int n, int64_t k, int level, const TR* __restrict__ R,
-                               const double* __restrict__ w, double* __restrict__ u) {
-    backsub_row_generic<TR>(n, k, level, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, R, w, u);
-}
 
 // R and SelInv-store access of the column-owner SelInv kernel: AoS rows by original index, or
 // the small-state path's per-level element-major rows.  part 0/1/2 = Rd/Rl/Rr; S part 0/1 = Sl/Sr.
@@ -215,173 +172,11 @@ __global__ void sum_kernel(const double* __restrict__ x, int64_t count, double* 
     if (threadIdx.x == 0) *out = part[0];
 }
 
-// q_i = K_i^{-1} (F_i u_i + c_i - H_i u_{i+1}) with K_i = L_K L_K^T (one thread per step).
-__device__ void refine_q_generic(const RefineArgs& a, int64_t i) {
-    if (i + 1 >= a.k) return;
-    const int n = a.n, nn = n * n;
-    const double* F = a.F + ti_step(a.ti, TI_F, i) * nn;
-    const double* H = a.H + ti_step(a.ti, TI_H, i) * nn;
-    const double* Lk = a.LK + i * nn;
-    const double* u0 = a.u + i * n;
-    const double* u1 = a.u + (i + 1) * n;
-    double e[KS_NMAX];
-    for (int r = 0; r < n; ++r) {
-        double s = a.c ? a.c[i * n + r] : 0.0;
-        for (int p = 0; p < n; ++p) s = fma(F[r * n + p], u0[p], s);
-        for (int p = 0; p < n; ++p) s = fma(-H[r * n + p], u1[p], s);
-        e[r] = s;
-    }
-    for (int r = 0; r < n; ++r) {  // L y = e
-        double s = e[r];
-        for (int p = 0; p < r; ++p) s = fma(-Lk[r * n + p], e[p], s);
-        e[r] = s / Lk[r * n + r];
-    }
-    for (int r = n - 1; r >= 0; --r) {  // L^T q = y
-        double s = e[r];
-        for (int p = r + 1; p < n; ++p) s = fma(-Lk[p * n + r], e[p], s);
-        e[r] = s / Lk[r * n + r];
-    }
-    for (int r = 0; r < n; ++r) a.q[i * n + r] = e[r];
-}
-
-__global__ void refine_q_kernel(RefineArgs a) {
-    refine_q_generic(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-}
-
-// g_c = H_{c-1}^T q_{c-1} - F_c^T q_c + G_c^T C_c^{-1} (o_c - G_c u_c).
-__device__ void refine_g_generic(const RefineArgs& a, int64_t c) {
-    if (c >= a.k) return;
-    const int n = a.n, nn = n * n;
-    double g[KS_NMAX];
-    for (int r = 0; r < n; ++r) g[r] = 0.0;
-    if (c >= 1) {
-        const double* H = a.H + ti_step(a.ti, TI_H, c - 1) * nn;
-        const double* qv = a.q + (c - 1) * n;
-        for (int r = 0; r < n; ++r)
-            for (int p = 0; p < n; ++p) g[r] = fma(H[p * n + r], qv[p], g[r]);
-    }
-    if (c + 1 < a.k) {
-        const double* F = a.F + ti_step(a.ti, TI_F, c) * nn;
-        const double* qv = a.q + c * n;
-        for (int r = 0; r < n; ++r)
-            for (int p = 0; p < n; ++p) g[r] = fma(-F[p * n + r], qv[p], g[r]);
-    }
-    int mi;
-    int64_t go, co;
-    if (a.m_uniform >= 0) {
-        mi = a.m_uniform;
-        go = c * mi;
-        co = c * (int64_t)mi * mi;
-    } else {
-        mi = a.m[c];
-        go = a.goff[c];
-        co = a.coff[c];
-    }
-    if (mi > 0) {
-        const double* G = a.G + ((a.ti & TI_G) ? 0 : go) * n;
-        const double* Lc = a.LC + co;
-        const double* uc = a.u + c * n;
-        double v[KS_NMAX];
-        for (int r = 0; r < mi; ++r) {
-            double s = a.o[go + r];
-            for (int p = 0; p < n; ++p) s = fma(-G[r * n + p], uc[p], s);
-            v[r] = s;
-        }
-        for (int r = 0; r < mi; ++r) {
-            double s = v[r];
-            for (int p = 0; p < r; ++p) s = fma(-Lc[r * mi + p], v[p], s);
-            v[r] = s / Lc[r * mi + r];
-        }
-        for (int r = mi - 1; r >= 0; --r) {
-            double s = v[r];
-            for (int p = r + 1; p < mi; ++p) s = fma(-Lc[p * mi + r], v[p], s);
-            v[r] = s / Lc[r * mi + r];
-        }
-        for (int r = 0; r < n; ++r)
-            for (int p = 0; p < mi; ++p) g[r] = fma(G[p * n + r], v[p], g[r]);
-    }
-    for (int r = 0; r < n; ++r) a.g[c * n + r] = g[r];
-}
-
-__global__ void refine_g_kernel(RefineArgs a) {
-    refine_g_generic(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
-}
-
-// R^T w = g at one level: every column alive at `level` first pulls the blocks of the rows
-// eliminated at level-1 that touch it (rows c -+ 2^{level-1}), then, if it is eliminated at
-// `level`, solves Rd_c^T w_c = g_c.
-template <typename TR>
-__device__ void rt_solve_generic(int n, int64_t k, int level, int64_t j, const TR* __restrict__ R,
-                                 double* __restrict__ g, double* __restrict__ w) {
-    if (j >= (k >> level)) return;
-    const int64_t c = ((j + 1) << level) - 1;
-    const int nn = n * n;
-    const int64_t RS = rstore_rs(n);
-    double r[KS_NMAX];
-    for (int i = 0; i < n; ++i) r[i] = g[c * n + i];
-    if (level >= 1) {
-        const int64_t h = 1LL << (level - 1);
-        if (c - h >= 0) {  // row c-h has its right block Rr at column c
-            const TR* Rr = R + (c - h) * RS + 2 * nn;
-            const double* wr = w + (c - h) * n;
-            for (int i = 0; i < n; ++i) {
-                double s = r[i];
-                for (int p = 0; p < n; ++p) s = fma(-(double)Rr[p * n + i], wr[p], s);
-                r[i] = s;
-            }
-        }
-        if (c + h < k) {  // row c+h has its left block Rl at column c
-            const TR* Rl = R + (c + h) * RS + nn;
-            const double* wr = w + (c + h) * n;
-            for (int i = 0; i < n; ++i) {
-                double s = r[i];
-                for (int p = 0; p < n; ++p) s = fma(-(double)Rl[p * n + i], wr[p], s);
-                r[i] = s;
-            }
-        }
-    }
-    if (ctz64(c + 1) == level) {
-        const TR* Rd = R + c * RS;
-        for (int i = 0; i < n; ++i) {
-            double s = r[i];
-            for (int p = 0; p < i; ++p) s = fma(-(double)Rd[p * n + i], r[p], s);
-            r[i] = s / (double)Rd[i * n + i];
-        }
-        for (int i = 0; i < n; ++i) w[c * n + i] = r[i];
-    } else {
-        for (int i = 0; i < n; ++i) g[c * n + i] = r[i];
-    }
-}
-
-template <typename TR>
-__global__ void rt_solve_kernel(int n, int64_t k, int level, const TR* __restrict__ R,
-                                double* __restrict__ g, double* __restrict__ w) {
-    rt_solve_generic<TR>(n, k, level, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, R, g, w);
-}
-
-__global__ void axpy_kernel(double* __restrict__ u, const double* __restrict__ d, int64_t count) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * blockDim.x)
-        u[i] += d[i];
-}
-
 static unsigned grid_for(int64_t work, int threads) {
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
     if (b > (1LL << 30)) b = 1LL << 30;
     return (unsigned)b;
-}
-
-cudaError_t launch_backsub(int n, int64_t k, int level, const void* R, const double* w,
-                           double* u, bool fp32, cudaStream_t st) {
-    const int64_t cols = ((k >> level) + 1) / 2;
-    const int threads = 128;
-    if (fp32)
-        backsub_kernel<float><<<grid_for(cols, threads), threads, 0, st>>>(n, k, level, (const float*)R, w, u);
-    else
-        backsub_kernel<double><<<grid_for(cols, threads), threads, 0, st>>>(n, k, level, (const double*)R, w, u);
-    ++t_launches;
-    return cudaGetLastError();
 }
 
 template <template <typename> class IO>
@@ -407,6 +202,7 @@ static cudaError_t launch_selinv_io(int n, int64_t k, int level, const void* R, 
 
 cudaError_t launch_selinv(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
                           unsigned long long* bad, bool fp32, cudaStream_t st) {
+    if (use_large(n, fp32)) return launch_selinv_large(n, k, level, R, Sx, Sd, bad, fp32, st);
     return launch_selinv_io<SelAos>(n, k, level, R, Sx, Sd, bad, fp32, st);
 }
 
@@ -435,256 +231,30 @@ cudaError_t launch_sum(const double* x, int64_t count, double* out, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_gradient(const RefineArgs& a, cudaStream_t st) {
-    if (a.k > 1) {
-        refine_q_kernel<<<grid_for(a.k - 1, 128), 128, 0, st>>>(a);
-        ++t_launches;
-    }
-    refine_g_kernel<<<grid_for(a.k, 128), 128, 0, st>>>(a);
-    ++t_launches;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_rt_solve(int n, int64_t k, int level, const void* R, double* g, double* w,
-                            bool fp32, cudaStream_t st) {
-    const int64_t cols = k >> level;
-    if (fp32)
-        rt_solve_kernel<float><<<grid_for(cols, 128), 128, 0, st>>>(n, k, level, (const float*)R, g, w);
-    else
-        rt_solve_kernel<double><<<grid_for(cols, 128), 128, 0, st>>>(n, k, level, (const double*)R, g, w);
-    ++t_launches;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_axpy(double* u, const double* d, int64_t count, cudaStream_t st) {
-    axpy_kernel<<<grid_for(count, 256) > 4096 ? 4096 : grid_for(count, 256), 256, 0, st>>>(u, d, count);
-    ++t_launches;
-    return cudaGetLastError();
-}
-
 // ---- warp-per-unit kernels of the column-owner path -----------------------------------------
-// One warp per block row / column / step; lane l owns rows l and l+32 (n <= 64).  Triangular
+// One warp per block row / column / step; lane l owns rows l, l+32, ... (ks_warp.cuh).  Triangular
 // substitutions proceed one unknown at a time: its owner lane divides and broadcasts it with a
 // shuffle, and every lane updates its own rows.  In FP32 + refinement mode the vectors are FP32
 // except the residuals of the refinement, which are formed in FP64.
 
-// Back substitution of block row q at `level`: u_c = Rd^{-1}(rhs - Rl u_a - Rr u_b).
-// rhs = y from the R store (w == nullptr) or w_c.  Vectors of type TV, output of type TO.
-template <typename TR, typename TV, typename TO>
-__device__ void backsub_warp(int n, int64_t k, int level, int64_t q, const TR* __restrict__ R,
-                             const TV* __restrict__ w, TO* __restrict__ u) {
-    const int lane = threadIdx.x & 31;
-    const int64_t c = ((2 * q + 1) << level) - 1;
-    if (c >= k) return;
-    const int nn = n * n;
-    const TR* Rc = R + c * rstore_rs(n);
-    const int64_t a = c - (1LL << level), b = c + (1LL << level);
-    TV r0 = TV(0), r1 = TV(0);
-    const int i0 = lane, i1 = lane + 32;
-    if (i0 < n) r0 = w ? w[c * n + i0] : (TV)Rc[3 * nn + i0];
-    if (i1 < n) r1 = w ? w[c * n + i1] : (TV)Rc[3 * nn + i1];
-    if (a >= 0) {
-        for (int p = 0; p < n; ++p) {
-            const TV up = (TV)u[a * n + p];
-            if (i0 < n) r0 = fma(-(TV)Rc[nn + i0 * n + p], up, r0);
-            if (i1 < n) r1 = fma(-(TV)Rc[nn + i1 * n + p], up, r1);
-        }
-    }
-    if (b < k) {
-        for (int p = 0; p < n; ++p) {
-            const TV up = (TV)u[b * n + p];
-            if (i0 < n) r0 = fma(-(TV)Rc[2 * nn + i0 * n + p], up, r0);
-            if (i1 < n) r1 = fma(-(TV)Rc[2 * nn + i1 * n + p], up, r1);
-        }
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        TV x = TV(0);
-        if ((i & 31) == lane) x = ((i < 32) ? r0 : r1) / (TV)Rc[i * n + i];
-        x = __shfl_sync(0xffffffffu, x, i & 31);
-        if (i0 < i) r0 = fma(-(TV)Rc[i0 * n + i], x, r0);
-        if (i1 < i) r1 = fma(-(TV)Rc[i1 * n + i], x, r1);
-        if (i0 == i) r0 = x;
-        if (i1 == i) r1 = x;
-    }
-    if (i0 < n) u[c * n + i0] = (TO)r0;
-    if (i1 < n) u[c * n + i1] = (TO)r1;
-}
-
-// R^T w = g at `level` for alive column j (pull the two rows eliminated at level-1 that touch
-// it, then solve with Rd^T if it is eliminated here).
-template <typename TR, typename TV>
-__device__ void rt_solve_warp(int n, int64_t k, int level, int64_t j, const TR* __restrict__ R,
-                              TV* __restrict__ g, TV* __restrict__ w) {
-    const int lane = threadIdx.x & 31;
-    if (j >= (k >> level)) return;
-    const int64_t c = ((j + 1) << level) - 1;
-    const int nn = n * n;
-    const int64_t RS = rstore_rs(n);
-    const int i0 = lane, i1 = lane + 32;
-    TV r0 = i0 < n ? g[c * n + i0] : TV(0), r1 = i1 < n ? g[c * n + i1] : TV(0);
-    if (level >= 1) {
-        const int64_t h = 1LL << (level - 1);
-        if (c - h >= 0) {
-            const TR* Rr = R + (c - h) * RS + 2 * nn;
-            const TV* wr = w + (c - h) * n;
-            for (int p = 0; p < n; ++p) {
-                const TV wp = wr[p];
-                if (i0 < n) r0 = fma(-(TV)Rr[p * n + i0], wp, r0);
-                if (i1 < n) r1 = fma(-(TV)Rr[p * n + i1], wp, r1);
-            }
-        }
-        if (c + h < k) {
-            const TR* Rl = R + (c + h) * RS + nn;
-            const TV* wr = w + (c + h) * n;
-            for (int p = 0; p < n; ++p) {
-                const TV wp = wr[p];
-                if (i0 < n) r0 = fma(-(TV)Rl[p * n + i0], wp, r0);
-                if (i1 < n) r1 = fma(-(TV)Rl[p * n + i1], wp, r1);
-            }
-        }
-    }
-    if (ctz64(c + 1) == level) {
-        const TR* Rd = R + c * RS;
-        for (int i = 0; i < n; ++i) {
-            TV x = TV(0);
-            if ((i & 31) == lane) x = ((i < 32) ? r0 : r1) / (TV)Rd[i * n + i];
-            x = __shfl_sync(0xffffffffu, x, i & 31);
-            if (i0 > i && i0 < n) r0 = fma(-(TV)Rd[i * n + i0], x, r0);
-            if (i1 > i && i1 < n) r1 = fma(-(TV)Rd[i * n + i1], x, r1);
-            if (i0 == i) r0 = x;
-            if (i1 == i) r1 = x;
-        }
-        if (i0 < n) w[c * n + i0] = r0;
-        if (i1 < n) w[c * n + i1] = r1;
-    } else {
-        if (i0 < n) g[c * n + i0] = r0;
-        if (i1 < n) g[c * n + i1] = r1;
-    }
-}
-
-// Warp-cooperative solves with an FP64 lower-triangular factor L (ld = dim), in type TV:
-// forward (L y = x) then backward (L^T z = y); x given per lane in rows lane, lane+32.
-template <typename TV>
-__device__ void llt_solve_warp(int dim, const double* __restrict__ Lf, TV& r0, TV& r1) {
-    const int lane = threadIdx.x & 31;
-    const int i0 = lane, i1 = lane + 32;
-    for (int i = 0; i < dim; ++i) {
-        TV x = TV(0);
-        if ((i & 31) == lane) x = ((i < 32) ? r0 : r1) / (TV)Lf[i * dim + i];
-        x = __shfl_sync(0xffffffffu, x, i & 31);
-        if (i0 > i && i0 < dim) r0 = fma(-(TV)Lf[i0 * dim + i], x, r0);
-        if (i1 > i && i1 < dim) r1 = fma(-(TV)Lf[i1 * dim + i], x, r1);
-        if (i0 == i) r0 = x;
-        if (i1 == i) r1 = x;
-    }
-    for (int i = dim - 1; i >= 0; --i) {
-        TV x = TV(0);
-        if ((i & 31) == lane) x = ((i < 32) ? r0 : r1) / (TV)Lf[i * dim + i];
-        x = __shfl_sync(0xffffffffu, x, i & 31);
-        if (i0 < i) r0 = fma(-(TV)Lf[i * dim + i0], x, r0);
-        if (i1 < i) r1 = fma(-(TV)Lf[i * dim + i1], x, r1);
-        if (i0 == i) r0 = x;
-        if (i1 == i) r1 = x;
-    }
-}
-
-// q_i = K_i^{-1} (F_i u_i + c_i - H_i u_{i+1}): the residual in FP64, the solve in TV.
-template <typename TV>
-__device__ void refine_q_warp(const RefineArgs& a, int64_t i, TV* __restrict__ q) {
-    if (i + 1 >= a.k) return;
-    const int lane = threadIdx.x & 31, n = a.n, nn = n * n;
-    const double* F = a.F + ti_step(a.ti, TI_F, i) * nn;
-    const double* H = a.H + ti_step(a.ti, TI_H, i) * nn;
-    double e0 = 0.0, e1 = 0.0;
-    const int i0 = lane, i1 = lane + 32;
-    if (i0 < n) e0 = a.c ? a.c[i * n + i0] : 0.0;
-    if (i1 < n) e1 = a.c ? a.c[i * n + i1] : 0.0;
-    for (int p = 0; p < n; ++p) {
-        const double u0 = a.u[i * n + p], u1 = a.u[(i + 1) * n + p];
-        if (i0 < n) e0 = fma(-H[i0 * n + p], u1, fma(F[i0 * n + p], u0, e0));
-        if (i1 < n) e1 = fma(-H[i1 * n + p], u1, fma(F[i1 * n + p], u0, e1));
-    }
-    TV r0 = (TV)e0, r1 = (TV)e1;
-    llt_solve_warp<TV>(n, a.LK + i * nn, r0, r1);
-    if (i0 < n) q[i * n + i0] = r0;
-    if (i1 < n) q[i * n + i1] = r1;
-}
-
-// g_c = H_{c-1}^T q_{c-1} - F_c^T q_c + G_c^T C_c^{-1} (o_c - G_c u_c), o - G u in FP64.
-template <typename TV>
-__device__ void refine_g_warp(const RefineArgs& a, int64_t c, const TV* __restrict__ q,
-                              TV* __restrict__ g) {
-    if (c >= a.k) return;
-    const int lane = threadIdx.x & 31, n = a.n, nn = n * n;
-    const int i0 = lane, i1 = lane + 32;
-    TV g0 = TV(0), g1 = TV(0);
-    if (c >= 1) {
-        const double* H = a.H + ti_step(a.ti, TI_H, c - 1) * nn;
-        for (int p = 0; p < n; ++p) {
-            const TV qp = q[(c - 1) * n + p];
-            if (i0 < n) g0 = fma((TV)H[p * n + i0], qp, g0);
-            if (i1 < n) g1 = fma((TV)H[p * n + i1], qp, g1);
-        }
-    }
-    if (c + 1 < a.k) {
-        const double* F = a.F + ti_step(a.ti, TI_F, c) * nn;
-        for (int p = 0; p < n; ++p) {
-            const TV qp = q[c * n + p];
-            if (i0 < n) g0 = fma(-(TV)F[p * n + i0], qp, g0);
-            if (i1 < n) g1 = fma(-(TV)F[p * n + i1], qp, g1);
-        }
-    }
-    int mi;
-    int64_t go, co;
-    if (a.m_uniform >= 0) {
-        mi = a.m_uniform;
-        go = c * mi;
-        co = c * (int64_t)mi * mi;
-    } else {
-        mi = a.m[c];
-        go = a.goff[c];
-        co = a.coff[c];
-    }
-    if (mi > 0) {
-        const double* G = a.G + ((a.ti & TI_G) ? 0 : go) * n;
-        double v0 = 0.0, v1 = 0.0;
-        if (i0 < mi) v0 = a.o[go + i0];
-        if (i1 < mi) v1 = a.o[go + i1];
-        for (int p = 0; p < n; ++p) {
-            const double up = a.u[c * n + p];
-            if (i0 < mi) v0 = fma(-G[i0 * n + p], up, v0);
-            if (i1 < mi) v1 = fma(-G[i1 * n + p], up, v1);
-        }
-        TV r0 = (TV)v0, r1 = (TV)v1;
-        llt_solve_warp<TV>(mi, a.LC + co, r0, r1);
-        for (int p = 0; p < mi; ++p) {
-            const TV vp = __shfl_sync(0xffffffffu, p < 32 ? r0 : r1, p & 31);
-            if (i0 < n) g0 = fma((TV)G[p * n + i0], vp, g0);
-            if (i1 < n) g1 = fma((TV)G[p * n + i1], vp, g1);
-        }
-    }
-    if (i0 < n) g[c * n + i0] = g0;
-    if (i1 < n) g[c * n + i1] = g1;
-}
-
-template <typename TR, typename TV, typename TO>
+template <int NR, typename TR, typename TV, typename TO>
 __global__ void __launch_bounds__(128) backsub_warp_kernel(int n, int64_t k, int level, const TR* R,
                                                            const TV* w, TO* u) {
     const int64_t q = blockIdx.x * 4LL + (threadIdx.x >> 5);
-    if (q < (k >> level) - (k >> (level + 1))) backsub_warp<TR, TV, TO>(n, k, level, q, R, w, u);
+    if (q < (k >> level) - (k >> (level + 1))) backsub_warp<NR, TR, TV, TO>(n, k, level, q, R, w, u);
 }
 
-template <typename TR, typename TV>
+template <int NR, typename TR, typename TV>
 __global__ void __launch_bounds__(128) rt_solve_warp_kernel(int n, int64_t k, int level, const TR* R,
                                                             TV* g, TV* w) {
-    rt_solve_warp<TR, TV>(n, k, level, blockIdx.x * 4LL + (threadIdx.x >> 5), R, g, w);
+    rt_solve_warp<NR, TR, TV>(n, k, level, blockIdx.x * 4LL + (threadIdx.x >> 5), R, g, w);
 }
 
-template <typename TV>
+template <int NR, typename TV>
 __global__ void __launch_bounds__(128) refine_qg_warp_kernel(RefineArgs a, int which, TV* q, TV* g) {
     const int64_t x = blockIdx.x * 4LL + (threadIdx.x >> 5);
-    if (which == 0) refine_q_warp<TV>(a, x, q);
-    else refine_g_warp<TV>(a, x, q, g);
+    if (which == 0) refine_q_warp<NR, TV>(a, x, q);
+    else refine_g_warp<NR, TV>(a, x, q, g);
 }
 
 template <typename TV>
@@ -699,35 +269,43 @@ static unsigned warps_grid(int64_t units) {
     return (unsigned)(b < 1 ? 1 : (b > (1LL << 30) ? (1LL << 30) : b));
 }
 
-cudaError_t launch_backsub_warp(int n, int64_t k, int level, const void* R, bool fp32,
-                                double* u, cudaStream_t st) {
+template <int NR>
+static cudaError_t backsub_warp_nr(int n, int64_t k, int level, const void* R, bool fp32, double* u,
+                                   cudaStream_t st) {
     const int64_t rows = (k >> level) - (k >> (level + 1));
     if (fp32)  // FP32 first solve; the refinement corrects it
-        backsub_warp_kernel<float, float, double><<<warps_grid(rows), 128, 0, st>>>(
+        backsub_warp_kernel<NR, float, float, double><<<warps_grid(rows), 128, 0, st>>>(
             n, k, level, (const float*)R, (const float*)nullptr, u);
     else
-        backsub_warp_kernel<double, double, double><<<warps_grid(rows), 128, 0, st>>>(
+        backsub_warp_kernel<NR, double, double, double><<<warps_grid(rows), 128, 0, st>>>(
             n, k, level, (const double*)R, (const double*)nullptr, u);
     ++t_launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine_warp(const RefineArgs& a, float* q, float* g, float* w, float* d,
-                               const void* R, int L, cudaStream_t st) {
+cudaError_t launch_backsub_warp(int n, int64_t k, int level, const void* R, bool fp32,
+                                double* u, cudaStream_t st) {
+    return n <= 64 ? backsub_warp_nr<2>(n, k, level, R, fp32, u, st)
+                   : backsub_warp_nr<4>(n, k, level, R, fp32, u, st);
+}
+
+template <int NR>
+static cudaError_t refine_warp_nr(const RefineArgs& a, float* q, float* g, float* w, float* d,
+                                  const void* R, int L, cudaStream_t st) {
     const int64_t k = a.k;
     const float* Rf = static_cast<const float*>(R);
     if (k > 1) {
-        refine_qg_warp_kernel<float><<<warps_grid(k - 1), 128, 0, st>>>(a, 0, q, g);
+        refine_qg_warp_kernel<NR, float><<<warps_grid(k - 1), 128, 0, st>>>(a, 0, q, g);
         ++t_launches;
     }
-    refine_qg_warp_kernel<float><<<warps_grid(k), 128, 0, st>>>(a, 1, q, g);
+    refine_qg_warp_kernel<NR, float><<<warps_grid(k), 128, 0, st>>>(a, 1, q, g);
     ++t_launches;
     for (int l = 0; l <= L; ++l) {
-        rt_solve_warp_kernel<float, float><<<warps_grid(k >> l), 128, 0, st>>>(a.n, k, l, Rf, g, w);
+        rt_solve_warp_kernel<NR, float, float><<<warps_grid(k >> l), 128, 0, st>>>(a.n, k, l, Rf, g, w);
         ++t_launches;
     }
     for (int l = L; l >= 0; --l) {
-        backsub_warp_kernel<float, float, float><<<warps_grid((k >> l) - (k >> (l + 1))), 128, 0, st>>>(
+        backsub_warp_kernel<NR, float, float, float><<<warps_grid((k >> l) - (k >> (l + 1))), 128, 0, st>>>(
             a.n, k, l, Rf, w, d);
         ++t_launches;
     }
@@ -739,8 +317,14 @@ cudaError_t launch_refine_warp(const RefineArgs& a, float* q, float* g, float* w
     return cudaGetLastError();
 }
 
+cudaError_t launch_refine_warp(const RefineArgs& a, float* q, float* g, float* w, float* d,
+                               const void* R, int L, cudaStream_t st) {
+    return a.n <= 64 ? refine_warp_nr<2>(a, q, g, w, d, R, L, st)
+                     : refine_warp_nr<4>(a, q, g, w, d, R, L, st);
+}
+
 // ---- batched column-owner launches ----------------------------------------------------------
-template <typename T, int OP>
+template <typename T, int OP, int NR>
 __global__ void __launch_bounds__(256) batch_generic_k(const BatchWork* wk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const BatchWork w = *wk;
@@ -773,21 +357,21 @@ __global__ void __launch_bounds__(256) batch_generic_k(const BatchWork* wk) {
                           reinterpret_cast<T*>(P.R), P.cn2, P.cd2, P.bad);
             __syncthreads();
         } else if constexpr (OP == B_BACKSUB) {
-            backsub_warp<T, T, double>(n, P.k, l, x, reinterpret_cast<const T*>(P.R), (const T*)nullptr, P.u);
+            backsub_warp<NR, T, T, double>(n, P.k, l, x, reinterpret_cast<const T*>(P.R), (const T*)nullptr, P.u);
         } else if constexpr (OP == B_SELINV) {
             selinv_cta_row<T, SelAos<T>>(n, P.k, l, x, reinterpret_cast<const T*>(P.R),
                                          reinterpret_cast<T*>(P.Sx), P.cov, P.bad,
                                          reinterpret_cast<T*>(smem_raw));
         } else if constexpr (OP == B_REFINE_Q) {
-            refine_q_warp<float>(refine_args_of(P), x, reinterpret_cast<float*>(P.q));
+            refine_q_warp<NR, float>(refine_args_of(P), x, reinterpret_cast<float*>(P.q));
         } else if constexpr (OP == B_REFINE_G) {
-            refine_g_warp<float>(refine_args_of(P), x, reinterpret_cast<const float*>(P.q),
+            refine_g_warp<NR, float>(refine_args_of(P), x, reinterpret_cast<const float*>(P.q),
                                  reinterpret_cast<float*>(P.g));
         } else if constexpr (OP == B_RT_SOLVE) {
-            rt_solve_warp<float, float>(n, P.k, l, x, reinterpret_cast<const float*>(P.R),
+            rt_solve_warp<NR, float, float>(n, P.k, l, x, reinterpret_cast<const float*>(P.R),
                                         reinterpret_cast<float*>(P.g), reinterpret_cast<float*>(P.w));
         } else if constexpr (OP == B_BACKSUB_W) {
-            backsub_warp<float, float, float>(n, P.k, l, x, reinterpret_cast<const float*>(P.R),
+            backsub_warp<NR, float, float, float>(n, P.k, l, x, reinterpret_cast<const float*>(P.R),
                                               reinterpret_cast<const float*>(P.w),
                                               reinterpret_cast<float*>(P.d));
         } else if constexpr (OP == B_ADD) {
@@ -796,44 +380,61 @@ __global__ void __launch_bounds__(256) batch_generic_k(const BatchWork* wk) {
     }
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int NR>
 static cudaError_t batch_generic_launch(const BatchWork* wk, unsigned grid, int threads, size_t smem,
                                         cudaStream_t st) {
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(batch_generic_k<T, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    batch_generic_k<T, OP><<<grid, threads, smem, st>>>(wk);
+        cudaFuncSetAttribute(batch_generic_k<T, OP, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    batch_generic_k<T, OP, NR><<<grid, threads, smem, st>>>(wk);
     ++t_launches;
     return cudaGetLastError();
 }
 
-template <typename T>
+// NR = 2: state dimensions up to 64 (every operation); NR = 4: up to 128 (the vector
+// operations only -- whitening, levels and SelInv of those sizes run the large-state kernels).
+template <typename T, int NR>
 static cudaError_t batch_generic_t(int op, int n, int mmax, const BatchWork* wk, unsigned grid,
                                    cudaStream_t st) {
-    const int wthreads = ((std::max(3 * n + 2, n + mmax) + 31) / 32) * 32;
-    const int lthreads = ((3 * n + 1 + 31) / 32) * 32;
+    if constexpr (NR == 2) {
+        const int wthreads = ((std::max(3 * n + 2, n + mmax) + 31) / 32) * 32;
+        const int lthreads = ((3 * n + 1 + 31) / 32) * 32;
+        switch (op) {
+            case B_WHITEN:
+                return batch_generic_launch<T, B_WHITEN, NR>(wk, grid, wthreads,
+                                                             sizeof(double) * (size_t)whiten_layout(n, mmax).total, st);
+            case B_LEVEL:
+                return batch_generic_launch<T, B_LEVEL, NR>(wk, grid, lthreads, sizeof(T) * (size_t)tile_layout(n).total, st);
+            case B_SELINV:
+                return batch_generic_launch<T, B_SELINV, NR>(wk, grid, 128, sizeof(T) * (size_t)selinv_layout(n).total, st);
+            default: break;
+        }
+    }
     switch (op) {
-        case B_WHITEN:
-            return batch_generic_launch<T, B_WHITEN>(wk, grid, wthreads,
-                                                     sizeof(double) * (size_t)whiten_layout(n, mmax).total, st);
-        case B_LEVEL:
-            return batch_generic_launch<T, B_LEVEL>(wk, grid, lthreads, sizeof(T) * (size_t)tile_layout(n).total, st);
-        case B_BASE: return batch_generic_launch<T, B_BASE>(wk, grid, 128, 0, st);
-        case B_BACKSUB: return batch_generic_launch<T, B_BACKSUB>(wk, grid, 128, 0, st);
-        case B_SELINV:
-            return batch_generic_launch<T, B_SELINV>(wk, grid, 128, sizeof(T) * (size_t)selinv_layout(n).total, st);
-        case B_REFINE_Q: return batch_generic_launch<T, B_REFINE_Q>(wk, grid, 128, 0, st);
-        case B_REFINE_G: return batch_generic_launch<T, B_REFINE_G>(wk, grid, 128, 0, st);
-        case B_RT_SOLVE: return batch_generic_launch<T, B_RT_SOLVE>(wk, grid, 128, 0, st);
-        case B_BACKSUB_W: return batch_generic_launch<T, B_BACKSUB_W>(wk, grid, 128, 0, st);
-        case B_ADD: return batch_generic_launch<T, B_ADD>(wk, grid, 256, 0, st);
+        case B_BASE: return batch_generic_launch<T, B_BASE, NR>(wk, grid, 128, 0, st);
+        case B_BACKSUB: return batch_generic_launch<T, B_BACKSUB, NR>(wk, grid, 128, 0, st);
+        case B_REFINE_Q: return batch_generic_launch<T, B_REFINE_Q, NR>(wk, grid, 128, 0, st);
+        case B_REFINE_G: return batch_generic_launch<T, B_REFINE_G, NR>(wk, grid, 128, 0, st);
+        case B_RT_SOLVE: return batch_generic_launch<T, B_RT_SOLVE, NR>(wk, grid, 128, 0, st);
+        case B_BACKSUB_W: return batch_generic_launch<T, B_BACKSUB_W, NR>(wk, grid, 128, 0, st);
+        case B_ADD: return batch_generic_launch<T, B_ADD, NR>(wk, grid, 256, 0, st);
+        default: break;
     }
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_batch_generic(int op, int n, int mmax, const BatchWork* wk, bool fp32,
                                  unsigned grid, cudaStream_t st) {
-    return fp32 ? batch_generic_t<float>(op, n, mmax, wk, grid, st)
-                : batch_generic_t<double>(op, n, mmax, wk, grid, st);
+    if (use_large(n, fp32) && (op == B_WHITEN || op == B_LEVEL || op == B_SELINV))
+        return launch_batch_large(op, n, wk, fp32, grid, st);
+    if (op == B_WHITEN && !generic_whiten_fits(n, mmax))
+        return launch_batch_large(op, n, wk, fp32, grid, st);
+    if (op == B_LEVEL)
+        if (const MedOps* m = med_ops(n, fp32)) return m->batch_level(wk, fp32, grid, st);
+    if (n <= 64)
+        return fp32 ? batch_generic_t<float, 2>(op, n, mmax, wk, grid, st)
+                    : batch_generic_t<double, 2>(op, n, mmax, wk, grid, st);
+    return fp32 ? batch_generic_t<float, 4>(op, n, mmax, wk, grid, st)
+                : batch_generic_t<double, 4>(op, n, mmax, wk, grid, st);
 }
 
 }  // namespace ks
