@@ -19,19 +19,25 @@ const SmallOps* small_ops(int n) {
 }
 
 extern const MedOps med_ops_12, med_ops_16, med_ops_24, med_ops_32, med_ops_48, med_ops_64;
-const MedOps* med_ops(int n, bool fp32) {
+static const MedOps* med_table(int n) {
     if (const char* v = getenv("KS_NO_MED")) { if (*v && *v != '0') return nullptr; }
-    const MedOps* m = nullptr;
     switch (n) {
-        case 12: m = &med_ops_12; break;
-        case 16: m = &med_ops_16; break;
-        case 24: m = &med_ops_24; break;
-        case 32: m = &med_ops_32; break;
-        case 48: m = &med_ops_48; break;
-        case 64: m = &med_ops_64; break;
+        case 12: return &med_ops_12;
+        case 16: return &med_ops_16;
+        case 24: return &med_ops_24;
+        case 32: return &med_ops_32;
+        case 48: return &med_ops_48;
+        case 64: return &med_ops_64;
         default: return nullptr;
     }
-    return (fp32 || m->fp64) ? m : nullptr;
+}
+const MedOps* med_ops(int n, bool fp32) {
+    const MedOps* m = med_table(n);
+    return (m != nullptr && (fp32 || m->fp64)) ? m : nullptr;
+}
+const MedOps* med_whiten_ops(int n, int mmax, bool fp32) {
+    const MedOps* m = med_table(n);
+    return (m != nullptr && mmax <= n && (fp32 || m->wfp64)) ? m : nullptr;
 }
 }  // namespace ks
 

@@ -396,17 +396,22 @@ struct SmallOps {
     cudaError_t (*batch)(int op, const BatchWork* wk, bool fp32, unsigned grid, cudaStream_t);
 };
 
-// Register-column level kernel of medium state dimensions (compiled for a few n); used in place
-// of the column-owner level kernel when med_ops(n, fp32) is not null.
+// Register-column level and whitening kernels of medium state dimensions (compiled for a few
+// n); used in place of the column-owner kernels when med_ops(n, fp32) (levels) or
+// med_whiten_ops(n, mmax, fp32) (whitening) is not null.
 struct MedOps {
     int n;
-    bool fp64;
+    bool fp64;             // FP64 levels compiled
     cudaError_t (*level)(int64_t nc, int level, int64_t k, const void* in, void* out, void* R,
                          double* resid, const double* cn2, const double* cd2,
                          unsigned long long* bad, bool fp32, cudaStream_t);
     cudaError_t (*batch_level)(const BatchWork* wk, bool fp32, unsigned grid, cudaStream_t);
+    bool wfp64;            // FP64 whitening compiled
+    cudaError_t (*whiten)(const WhitenArgs& a, bool fp32, cudaStream_t);
+    cudaError_t (*batch_whiten)(const BatchWork* wk, bool fp32, unsigned grid, cudaStream_t);
 };
 const MedOps* med_ops(int n, bool fp32);
+const MedOps* med_whiten_ops(int n, int mmax, bool fp32);
 
 // Batched column-owner launches (classes with n > 8 or some m_i > n).
 cudaError_t launch_batch_generic(int op, int n, int mmax, const BatchWork* wk, bool fp32,

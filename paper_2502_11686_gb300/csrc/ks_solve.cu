@@ -426,6 +426,8 @@ cudaError_t launch_batch_generic(int op, int n, int mmax, const BatchWork* wk, b
                                  unsigned grid, cudaStream_t st) {
     if (use_large(n, fp32) && (op == B_WHITEN || op == B_LEVEL || op == B_SELINV))
         return launch_batch_large(op, n, wk, fp32, grid, st);
+    if (op == B_WHITEN)
+        if (const MedOps* m = med_whiten_ops(n, mmax, fp32)) return m->batch_whiten(wk, fp32, grid, st);
     if (op == B_WHITEN && !generic_whiten_fits(n, mmax))
         return launch_batch_large(op, n, wk, fp32, grid, st);
     if (op == B_LEVEL)

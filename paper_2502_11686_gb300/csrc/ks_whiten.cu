@@ -22,6 +22,8 @@ __global__ void __launch_bounds__(256) whiten_kernel(WhitenArgs a) {
 }
 
 cudaError_t launch_whiten(const WhitenArgs& a, bool fp32, cudaStream_t st) {
+    if (!use_large(a.n, fp32))
+        if (const MedOps* m = med_whiten_ops(a.n, a.mmax, fp32)) return m->whiten(a, fp32, st);
     if (use_large(a.n, fp32) || !generic_whiten_fits(a.n, a.mmax)) return launch_whiten_large(a, fp32, st);
     const WhitenLayout L = whiten_layout(a.n, a.mmax);
     const size_t smem = sizeof(double) * (size_t)L.total;

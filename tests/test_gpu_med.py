@@ -1,10 +1,13 @@
-"""Parity of the register-column level kernel (state dimensions 12, 16, 24, 32, 48, 64) with the
-oracle, and with the column-owner level kernel it replaces (KS_NO_MED=1 selects the latter).
+"""Parity of the register-column level and whitening kernels (state dimensions 12, 16, 24, 32, 48,
+64) with the oracle, and with the column-owner kernels they replace (KS_NO_MED=1 selects the
+latter).
 
 The lengths give levels of odd and even width (the three-block tail of Section 3), ragged
-observation counts run through the same kernel, and the residual (the discarded rows) must match
-too.  FP64 runs for n <= 32 (larger n have no FP64 build of this kernel and fall back to the
-column-owner kernel, which is checked by the same test); FP32 + refinement for all six.
+observation counts (including steps without observations) run through the same kernels, and the
+residual (the discarded rows) must match too.  Levels run in FP64 for n <= 32 and whitening for
+n <= 48 (larger n fall back to the column-owner kernels, which the same test checks); FP32 +
+refinement for all six.  Steps with more observations than the state dimension take the
+column-owner whitening.
 """
 import numpy as np
 import pytest
@@ -59,15 +62,42 @@ def test_med_kernel_matches_oracle_and_column_owner(n, k, precision, monkeypatch
         assert abs(r2 - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"])
 
 
-@pytest.mark.parametrize("n", [12, 32])
-def test_med_kernel_ragged_observations(n):
+@pytest.mark.parametrize("n,precision", [(12, "fp64"), (32, "fp64"), (48, "fp64"),
+                                         (16, "fp32_refine"), (48, "fp32_refine")])
+def test_med_kernel_ragged_observations(n, precision, monkeypatch):
     rng = np.random.default_rng(n)
     k = 150
     m = rng.integers(0, n + 1, size=k).astype(np.int32)
     m[0] = n
+    m[5] = 0
     p = inputs.random_problem(k, n, m, seed=5 + n, with_c=False)
     ref = oracle.smooth(p)
-    with Smoother(device=0, precision="fp64") as sm:
-        u, cov, _ = run(sm, p)
-    assert rel(u, ref["u"]) < 1e-10
-    assert rel_blocks(cov, ref["cov"]) < 1e-10
+    with Smoother(device=0, precision=precision) as sm:
+        monkeypatch.setenv("KS_NO_MED", "0")
+        u, cov, r2 = run(sm, p)
+        monkeypatch.setenv("KS_NO_MED", "1")
+        u0, cov0, _ = run(sm, p)
+    tol_u = 1e-10 if precision == "fp64" else 1e-6
+    tol_c = 1e-10 if precision == "fp64" else 1e-3
+    assert rel(u, ref["u"]) < tol_u
+    assert rel_blocks(cov, ref["cov"]) < tol_c
+    assert rel(u, u0) < tol_u
+    assert rel_blocks(cov, cov0) < tol_c
+    if precision == "fp64":
+        assert abs(r2 - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_med_whitening_falls_back_for_wide_steps(precision):
+    """Steps with m_i > n exceed the register-column whitening; the column-owner kernel runs."""
+    n, k = 16, 90
+    m = np.full(k, n // 2, dtype=np.int32)
+    m[::7] = n + 5
+    p = inputs.random_problem(k, n, m, seed=41, with_c=True)
+    ref = oracle.smooth(p)
+    with Smoother(device=0, precision=precision) as sm:
+        u, cov, r2 = run(sm, p)
+    assert rel(u, ref["u"]) < (1e-10 if precision == "fp64" else 1e-6)
+    assert rel_blocks(cov, ref["cov"]) < (1e-10 if precision == "fp64" else 1e-3)
+    if precision == "fp64":
+        assert abs(r2 - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"])
