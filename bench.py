@@ -45,6 +45,9 @@ WORKLOADS = {
     "dense_k1e5_n48": dict(k=100_000, n=48, m=48, f_scale=0.995, sample_k=1500, ref_sample_k=300,
                            desc="k=100,000 states, n=m=48, F=0.995*orth, H=I, G~N(0,1/48), "
                                 "K,C=LL^T per step; states + all covariances"),
+    "large_k1e4_n128": dict(k=10_000, n=128, m=128, f_scale=0.995, sample_k=200, ref_sample_k=60,
+                            desc="k=10,000 states, n=m=128, F=0.995*orth, H=I, G~N(0,1/128), "
+                                 "K,C=LL^T per step; states + all covariances"),
 }
 
 

@@ -1,5 +1,9 @@
-"""Hardware probes.  ``python -m paper_2502_11686_gb300.probes`` compiles fma_probe.cu for
-sm_103a next to this file and prints the DFMA / FFMA rates it measures."""
+"""Hardware probes, compiled for sm_103a next to this file.
+
+``python -m paper_2502_11686_gb300.probes`` prints the DFMA / FFMA rates fma_probe.cu measures;
+``python -m paper_2502_11686_gb300.probes tc`` runs tc_probe.cu, which checks the tcgen05
+conventions of the tensor-core kernels (TMEM layouts, descriptors, 3xTF32) against an FP64
+product and exits non-zero on a mismatch."""
 import os
 import subprocess
 import sys
@@ -13,6 +17,14 @@ def run_fma_probe() -> str:
     exe = os.path.join(HERE, "fma_probe")
     subprocess.check_call([nvcc(), "-O3", GENCODE, "-o", exe, src])
     return subprocess.check_output([exe], text=True)
+
+
+def run_tc_probe() -> int:
+    from ..build import GENCODE, INCLUDE, nvcc
+    src = os.path.join(HERE, "tc_probe.cu")
+    exe = os.path.join(HERE, "tc_probe")
+    subprocess.check_call([nvcc(), "-O3", GENCODE, "-I", INCLUDE, "-o", exe, src])
+    return subprocess.call([exe])
 
 
 if __name__ == "__main__":
