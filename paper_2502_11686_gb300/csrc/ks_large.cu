@@ -23,7 +23,22 @@
 //     M = Ri - [Sl | Sr] A^T -> the covariance slot of c
 //     S_cc = M Ri^T         in place, one row block at a time, then symmetrised,
 //   which is S_cc = Ri Ri^T - [Sl | Sr] T^T with T = Ri A, the form of Algorithm 2.
+//
+// FP32 trailing updates on the tensor cores (tcgen05, 3xTF32; ks_tc.cuh).  With the panel's
+// compact-WY factor I - V T V^T, a chunk of up to 128 trailing columns X = [Xt ; Xb] is
+// updated as
+//     W1 = Xt + V^T Xb      tensor cores: D1 = Xb^T V, Xb^T staged in TMEM (lane = column),
+//                           V^T in shared memory; M = 128, N = 32, K = p
+//     W2 = T^T W1           CUDA cores, one thread per column (32 x 32 triangle)
+//     Xt -= W2; Xb -= V W2  tensor cores: D2 = V W2, V and W2^T in shared memory; M = 128,
+//                           N = chunk width, K = 32
+// with FP32 accumulators in TMEM (512 columns per block: Xb^T hi | lo, D1, D2).  Each product
+// is the sum of the hi.lo, lo.hi and hi.hi TF32 products, which keeps FP32 accuracy.  Chunks
+// narrower than 16 columns (the right-hand side) stay on the CUDA-core update.  The MMAs are
+// issued by one thread and complete through an mbarrier; every wait is bounded and a timeout
+// sets ST_TIMEOUT, stops further tensor-core work and still frees the TMEM.
 #include "ks_internal.cuh"
+#include "ks_tc.cuh"
 
 namespace ks {
 namespace large {
@@ -33,6 +48,7 @@ constexpr int PB = 32;     // reflectors per panel
 constexpr int CW = 32;     // columns per trailing-update chunk
 constexpr int PMAX = LARGE_NMAX;
 constexpr int LDV = PB + 1;
+static_assert(NTH == 8 * PB && PMAX % 8 == 0, "the register panel gives each column 8 threads");
 
 // Shared memory of the blocked QR (elements of T).
 struct QrSmem {
@@ -64,32 +80,6 @@ __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-
-// Reflector of panel column i (one warp): alpha = Tp[i][i], x = Vb[:, i] (p rows).  Scales the
-// full-block part to v (unit leading entry implied), sets Tp[i][i] = beta and tau[i].
-template <typename T>
-__device__ __forceinline__ void form_reflector(T* sm, int i, int p) {
-    T* Vb = sm + QrSmem::VB;
-    T* Tp = sm + QrSmem::TP;
-    const int lane = threadIdx.x & 31;
-    T s = T(0);
-    for (int r = lane; r < p; r += 32) s = fma(Vb[r * LDV + i], Vb[r * LDV + i], s);
-    const T sigma = warp_sum(s);
-    const T alpha = Tp[i * LDV + i];
-    const bool ok = sigma != T(0);
-    T g = T(0), tau = T(0), beta = alpha;
-    if (ok) {
-        const T nrm = sqrt(fma(alpha, alpha, sigma));
-        beta = alpha >= T(0) ? -nrm : nrm;
-        g = T(1) / (alpha - beta);
-        tau = (beta - alpha) / beta;
-    }
-    for (int r = lane; r < p; r += 32) Vb[r * LDV + i] *= g;
-    if (lane == 0) {
-        Tp[i * LDV + i] = beta;
-        sm[QrSmem::TAU + i] = tau;
-    }
 }
 
 // Trailing update of columns [c0, c0 + w) of block B by the panel's reflectors (top rows
@@ -162,10 +152,299 @@ __device__ void apply_chunk(const Blk<T>& B, int c0, int w, int kk0, int bw, int
     __syncthreads();
 }
 
+// ------------------------------------------------------------------------------------------
+// Tensor-core state of a block (FP32 kernels).
+struct TcSmem {   // byte offsets inside the block's tensor-core region
+    static constexpr int B1 = 0;           // [V^T hi ; V^T lo], 64 x 128 tile (rows q | 32 + q, depth r)
+    static constexpr int A2H = 32768;      // V, 128 x 32 tile (rows r, depth q), hi
+    static constexpr int A2L = 49152;      //   lo
+    static constexpr int B2H = 65536;      // W2^T, 128 x 32 tile (rows c, depth q), hi
+    static constexpr int B2L = 81920;      //   lo
+    static constexpr int MBAR = 98304;     // MMA completion barrier
+    static constexpr int SLOT = 98312;     // TMEM address written by the allocation
+    static constexpr int ABORT = 98316;    // set after a timed-out wait
+    static constexpr int BYTES = 98320;
+};
+// TMEM columns: Xb^T hi | lo (A of the first product), D1 = [Xb^T_hi V_hi + Xb^T_lo V_hi |
+// Xb^T_hi V_lo] (64 columns), D2 (up to 128 columns).
+constexpr uint32_t TM_A1H = 0, TM_A1L = 128, TM_D1 = 256, TM_D2 = 384, TM_COLS = 512;
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 20;   // polls; about a second at most
+constexpr int TC_CW = 128;                 // columns per tensor-core chunk
+
+struct TcState {
+    unsigned char* smem;                   // the region (TcSmem)
+    uint32_t tmem;                         // first of TM_COLS allocated columns
+    uint32_t phase;                        // parity of the next completion to wait for
+    unsigned long long* bad;               // error words for ST_TIMEOUT
+};
+
+__host__ __device__ inline size_t tc_align(size_t b) { return (b + 127) & ~(size_t)127; }
+
+// Whole block: allocate TMEM (warp 0), initialise the completion barrier.
+__device__ void tc_setup(TcState& tc, unsigned char* region, unsigned long long* bad) {
+    tc.smem = region;
+    tc.phase = 0;
+    tc.bad = bad;
+    uint32_t* slot = reinterpret_cast<uint32_t*>(region + TcSmem::SLOT);
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(slot, TM_COLS);
+        tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        tc::mbar_init(reinterpret_cast<uint64_t*>(region + TcSmem::MBAR), 1);
+        *reinterpret_cast<int*>(region + TcSmem::ABORT) = 0;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    tc.tmem = *slot;
+}
+
+// Whole block, after its last tensor-core operation.
+__device__ void tc_teardown(TcState& tc) {
+    tc::fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(tc.tmem, TM_COLS);
+}
+
+// Whole block: wait for the last commit (bounded), then a barrier.  A timeout anywhere sets the
+// abort flag (no further MMAs or waits) and ST_TIMEOUT.
+__device__ void tc_wait(TcState& tc) {
+    int* abort = reinterpret_cast<int*>(tc.smem + TcSmem::ABORT);
+    bool ok = true;
+    if (!*abort)
+        ok = tc::mbar_wait(reinterpret_cast<uint64_t*>(tc.smem + TcSmem::MBAR), tc.phase, TC_WAIT_LIMIT);
+    tc.phase ^= 1u;
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) {
+        if (!*abort && tc.bad != nullptr) flag_error(tc.bad, ST_TIMEOUT, 0);
+        *abort = 1;
+    }
+    tc::fence_after();
+}
+
+// The panel's V (p x bw in QrSmem::VB, zero-padded to 128 x 32) as the two shared-memory
+// operands: B1 = [V^T hi ; V^T lo] (rows q and 32 + q, depth r) and A2 = V (rows r, depth q),
+// the latter split hi | lo.
+__device__ void tc_panel_prep(int p, int bw, const float* sm, TcState& tc) {
+    const float* Vb = sm + QrSmem::VB;
+    float* b1 = reinterpret_cast<float*>(tc.smem + TcSmem::B1);
+    float* a2h = reinterpret_cast<float*>(tc.smem + TcSmem::A2H);
+    float* a2l = reinterpret_cast<float*>(tc.smem + TcSmem::A2L);
+    for (int e = threadIdx.x; e < 128 * PB; e += NTH) {
+        const int q = e >> 7, r = e & 127;
+        const float x = (r < p && q < bw) ? Vb[r * LDV + q] : 0.f;
+        const float h = tc::tf32_hi(x), l = x - h;
+        const uint32_t ia = tc::tile_off(128, r, q) >> 2;
+        a2h[ia] = h;
+        a2l[ia] = l;
+        b1[tc::tile_off(2 * PB, q, r) >> 2] = h;
+        b1[tc::tile_off(2 * PB, PB + q, r) >> 2] = l;
+    }
+    tc::fence_proxy_async_smem();
+}
+
+// A chunk of up to TC_CW trailing columns gathered from up to TC_SEGS column ranges of the
+// blocks a panel updates (the rest of the factor, the companions, the right-hand side).
+constexpr int TC_SEGS = 4;
+struct TcChunk {
+    int nseg, w;
+    Blk<float> b[TC_SEGS];
+    int c0[TC_SEGS];            // first column of segment s inside its block
+    int off[TC_SEGS + 1];       // first chunk column of segment s; off[nseg] = w
+};
+
+// Block and in-block column of chunk column c (c < w).
+__device__ __forceinline__ int tc_seg(const TcChunk& ch, int c) {
+    int s = 0;
+#pragma unroll
+    for (int q = 1; q < TC_SEGS; ++q)
+        if (q < ch.nseg && c >= ch.off[q]) s = q;
+    return s;
+}
+
+// Part [J0, J1) of the first epilogue for chunk column c (see tc_apply_chunk): W2^T[c][j] =
+// sum_{q <= j} W1^T[c][q] T[q][j], Xt[j][c] -= W2^T[c][j], and W2^T[c][j] (hi | lo) into the B2
+// tile.  J0 and J1 are multiples of 4.
+template <int J0, int J1>
+__device__ __forceinline__ void tc_epi1_part(const float (&v)[32], const float (&xt)[32], bool live,
+                                             float* top, int64_t ldt, int kk0, int bw, int c,
+                                             const float* Tm, float* b2h, float* b2l) {
+    float w2[J1 - J0];
+#pragma unroll
+    for (int j = J0; j < J1; ++j) {
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int q = 0; q <= j; ++q) {
+            if (q & 1) a1 = fma(v[q], Tm[q * LDV + j], a1);
+            else a0 = fma(v[q], Tm[q * LDV + j], a0);
+        }
+        w2[j - J0] = a0 + a1;
+    }
+    if (live) {
+#pragma unroll
+        for (int j = J0; j < J1; ++j)
+            if (j < bw) top[(int64_t)(kk0 + j) * ldt] = xt[j] - w2[j - J0];
+    }
+#pragma unroll
+    for (int j = J0; j < J1; j += 4) {
+        float4 h4, l4;
+        h4.x = tc::tf32_hi(w2[j - J0]);     l4.x = w2[j - J0] - h4.x;
+        h4.y = tc::tf32_hi(w2[j - J0 + 1]); l4.y = w2[j - J0 + 1] - h4.y;
+        h4.z = tc::tf32_hi(w2[j - J0 + 2]); l4.z = w2[j - J0 + 2] - h4.z;
+        h4.w = tc::tf32_hi(w2[j - J0 + 3]); l4.w = w2[j - J0 + 3] - h4.w;
+        const uint32_t o = tc::tile_off(128, c, j) >> 2;
+        *reinterpret_cast<float4*>(b2h + o) = h4;
+        *reinterpret_cast<float4*>(b2l + o) = l4;
+    }
+}
+
+// Trailing update of the chunk's columns by the panel whose reflectors are rows kk0 .. kk0 +
+// bw - 1 of the triangle part (see the file comment).  Whole block.
+__device__ void tc_apply_chunk(const TcChunk& ch, int kk0, int bw, int p, const float* sm, TcState& tc) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q4 = warp & 3, half = warp >> 2;
+    const uint32_t lanes = (uint32_t)(32 * q4) << 16;
+    const int w = ch.w;
+    const int KP = (p + 7) & ~7;
+    const int NP = (w + 15) & ~15;
+    const int* abort = reinterpret_cast<const int*>(tc.smem + TcSmem::ABORT);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(tc.smem + TcSmem::MBAR);
+    const float* Tm = sm + QrSmem::TM;
+    // Thread-column c = 32 q4 + lane (the same column for both warp halves): its block column.
+    const int c = 32 * q4 + lane;
+    const bool live = c < w;
+    const int sg = live ? tc_seg(ch, c) : 0;
+    const int cc = live ? ch.c0[sg] + (c - ch.off[sg]) : 0;
+    // 1. Xb^T into TMEM: lane c = chunk column c, columns r (hi at TM_A1H, lo at TM_A1L); the
+    //    warp halves take alternate 32-row pieces, all loads of a warp issued before its stores.
+    {
+        const float* col = live ? ch.b[sg].bot + cc : nullptr;
+        const int64_t ldb = live ? ch.b[sg].ldb : 0;
+        float x0[32], x1[32];
+        const int pa = half, pb = half + 2;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int ra = pa * 32 + j, rb = pb * 32 + j;
+            x0[j] = (live && ra < p) ? col[(int64_t)ra * ldb] : 0.f;
+            x1[j] = (live && rb < p) ? col[(int64_t)rb * ldb] : 0.f;
+        }
+        float h[32], l[32];
+        if (pa * 32 < KP) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                h[j] = tc::tf32_hi(x0[j]);
+                l[j] = x0[j] - h[j];
+            }
+            tc::tmem_st32(tc.tmem + lanes + TM_A1H + (uint32_t)(pa * 32), h);
+            tc::tmem_st32(tc.tmem + lanes + TM_A1L + (uint32_t)(pa * 32), l);
+        }
+        if (pb * 32 < KP) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                h[j] = tc::tf32_hi(x1[j]);
+                l[j] = x1[j] - h[j];
+            }
+            tc::tmem_st32(tc.tmem + lanes + TM_A1H + (uint32_t)(pb * 32), h);
+            tc::tmem_st32(tc.tmem + lanes + TM_A1L + (uint32_t)(pb * 32), l);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    // 2. D1 (M = 128 columns c, K = KP rows): one N = 64 product Xb^T_hi [V_hi | V_lo] and one
+    //    N = 32 product Xb^T_lo V_hi into its first 32 columns, per K = 8 step.
+    if (tid == 0 && !*abort) {
+        tc::fence_after();
+        const uint32_t id64 = tc::idesc_tf32(128, 2 * PB), id32 = tc::idesc_tf32(128, PB);
+        const uint64_t b0 = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::B1), 2 * PB, 0);
+        const uint32_t d1 = tc.tmem + TM_D1;
+        for (int s = 0; s < KP / 8; ++s) {
+            const uint64_t bd = b0 + (uint64_t)((32 * 2 * PB * s) >> 4);
+            tc::mma_ts(d1, tc.tmem + TM_A1H + 8 * s, bd, id64, s > 0 ? 1u : 0u);
+            tc::mma_ts(d1, tc.tmem + TM_A1L + 8 * s, bd, id32, 1u);
+        }
+        tc::commit(mbar);
+    }
+    tc_wait(tc);
+    // 3. W1 = Xt + D1^T (both halves of every warp group hold the column's 32 values), then
+    //    W2^T = W1^T T split over the halves: j < 24 and j >= 24.
+    {
+        float* top = live ? ch.b[sg].top + cc : nullptr;
+        const int64_t ldt = live ? ch.b[sg].ldt : 0;
+        float v[32], v2[32];
+        tc::tmem_ld32(tc.tmem + lanes + TM_D1, v);
+        tc::tmem_ld32(tc.tmem + lanes + TM_D1 + PB, v2);
+        float xt[32];
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            xt[q] = (live && q < bw) ? top[(int64_t)(kk0 + q) * ldt] : 0.f;
+            v[q] += v2[q] + xt[q];
+        }
+        float* b2h = reinterpret_cast<float*>(tc.smem + TcSmem::B2H);
+        float* b2l = reinterpret_cast<float*>(tc.smem + TcSmem::B2L);
+        if (half == 0) tc_epi1_part<0, 24>(v, xt, live, top, ldt, kk0, bw, c, Tm, b2h, b2l);
+        else tc_epi1_part<24, 32>(v, xt, live, top, ldt, kk0, bw, c, Tm, b2h, b2l);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    // 4. D2 = V W2 (M = 128 rows r, N = NP columns, K = 32).
+    if (tid == 0 && !*abort) {
+        tc::fence_after();
+        const uint32_t id = tc::idesc_tf32(128, NP);
+        const uint64_t ah = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::A2H), 128, 0);
+        const uint64_t al = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::A2L), 128, 0);
+        const uint64_t bh = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::B2H), 128, 0);
+        const uint64_t bl = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::B2L), 128, 0);
+        const uint32_t d2 = tc.tmem + TM_D2;
+        for (int s = 0; s < PB / 8; ++s) {
+            const uint64_t st = (uint64_t)((32 * 128 * s) >> 4);
+            tc::mma_ss(d2, al + st, bh + st, id, s > 0 ? 1u : 0u);
+            tc::mma_ss(d2, ah + st, bl + st, id, 1u);
+            tc::mma_ss(d2, ah + st, bh + st, id, 1u);
+        }
+        tc::commit(mbar);
+    }
+    tc_wait(tc);
+    // 5. Xb -= D2.  Warp (q4, half) owns rows 32 q4 .. 32 q4 + 31 and the columns of its half;
+    //    each 32 x 32 piece read from TMEM (thread = row) is transposed through the free B2 tile
+    //    (XOR swizzle, no bank conflicts) so that the read-modify-write of Xb runs along rows,
+    //    lane = column.
+    {
+        float* S = reinterpret_cast<float*>(tc.smem + TcSmem::B2H) + warp * 1024;   // 32 x 32
+        const int cl0 = half * 64;
+        for (int cb = cl0; cb < cl0 + 64 && cb < NP; cb += 32) {
+            float v[32];
+            tc::tmem_ld32(tc.tmem + lanes + TM_D2 + (uint32_t)cb, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) S[lane * 32 + (j ^ lane)] = v[j];
+            __syncwarp();
+            // lane = chunk column cb + lane: its block and in-block column
+            const int cj = cb + lane;
+            const bool cl = cj < w;
+            const int sj = cl ? tc_seg(ch, cj) : 0;
+            float* base = cl ? ch.b[sj].bot + ch.c0[sj] + (cj - ch.off[sj]) : nullptr;
+            const int64_t ldb = cl ? ch.b[sj].ldb : 0;
+            const int r0 = 32 * q4;
+            float xo[32];
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr)
+                xo[rr] = (cl && r0 + rr < p) ? base[(int64_t)(r0 + rr) * ldb] : 0.f;
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr)
+                if (cl && r0 + rr < p) base[(int64_t)(r0 + rr) * ldb] = xo[rr] - S[rr * 32 + (lane ^ rr)];
+            __syncwarp();
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+}
+
 // Blocked "triangle over full block" QR: F.top (n x n, upper triangular) over F.bot (p x n),
 // applied to the companion blocks C[0 .. nc).  On return F.top holds R; F.bot is consumed.
+// With tc (FP32 only) the trailing updates run on the tensor cores.
 template <typename T>
-__device__ void tpqrt_wy(int n, int p, const Blk<T>& F, const Blk<T>* C, int nc, T* sm) {
+__device__ void tpqrt_wy(int n, int p, const Blk<T>& F, const Blk<T>* C, int nc, T* sm,
+                         TcState* tc = nullptr) {
     T* Vb = sm + QrSmem::VB;
     T* Tp = sm + QrSmem::TP;
     T* Tm = sm + QrSmem::TM;
@@ -184,22 +463,72 @@ __device__ void tpqrt_wy(int n, int p, const Blk<T>& F, const Blk<T>* C, int nc,
             Tp[i * LDV + j] = (i < bw && j < bw && i <= j) ? F.top[(int64_t)(kk0 + i) * F.ldt + kk0 + j] : T(0);
         }
         __syncthreads();
-        if (warp == 0) form_reflector<T>(sm, 0, p);
-        // Panel: reflector i applied to panel columns > i (column jj belongs to warp jj % 8);
-        // the owner of column i + 1 forms the next reflector right after updating it.
-        for (int i = 0; i < bw; ++i) {
-            __syncthreads();
-            const T tau = sm[QrSmem::TAU + i];
-            for (int jj = i + 1 + ((warp - (i + 1)) & 7); jj < bw; jj += 8) {
-                T s = T(0);
-                for (int r = lane; r < p; r += 32) s = fma(Vb[r * LDV + i], Vb[r * LDV + jj], s);
-                const T dot = warp_sum(s) + Tp[i * LDV + jj];
-                const T sc = tau * dot;
-                for (int r = lane; r < p; r += 32) Vb[r * LDV + jj] = fma(-sc, Vb[r * LDV + i], Vb[r * LDV + jj]);
-                __syncwarp();
-                if (lane == 0) Tp[i * LDV + jj] -= sc;
-                __syncwarp();
-                if (jj == i + 1) form_reflector<T>(sm, jj, p);
+        // Panel, register form: thread t works on panel column j = t / 8 and holds the rows
+        // r = t % 8 + 8 s (s < PMAX / 8) of the full block.  Reflector i: the eight threads of
+        // column i form it and publish v (double-buffered, so one barrier per reflector); every
+        // later column applies it at once (16-term partial dots, a three-step group reduction)
+        // and recomputes its |x|^2 for when its own turn comes.
+        {
+            constexpr int RS = PMAX / 8;
+            const int j = tid >> 3, sub = tid & 7;
+            T* XV = sm + QrSmem::XT;   // [2][PMAX] (the chunk buffers are free during the panel)
+            auto gsum = [](T v) {
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                return v;
+            };
+            T x[RS];
+            T a0 = T(0);
+#pragma unroll
+            for (int s2 = 0; s2 < RS; ++s2) {
+                const int r = sub + 8 * s2;
+                x[s2] = (r < p && j < bw) ? Vb[r * LDV + j] : T(0);
+                a0 = fma(x[s2], x[s2], a0);
+            }
+            T sig = gsum(a0);
+            for (int i = 0; i < bw; ++i) {
+                T* v = XV + (i & 1) * PMAX;
+                if (j == i) {
+                    const T alpha = Tp[i * LDV + i];
+                    T g = T(0), tau = T(0), beta = alpha;
+                    if (sig != T(0)) {
+                        const T nrm = sqrt(fma(alpha, alpha, sig));
+                        beta = alpha >= T(0) ? -nrm : nrm;
+                        g = T(1) / (alpha - beta);
+                        tau = (beta - alpha) / beta;
+                    }
+#pragma unroll
+                    for (int s2 = 0; s2 < RS; ++s2) {
+                        x[s2] *= g;
+                        v[sub + 8 * s2] = x[s2];
+                    }
+                    if (sub == 0) {
+                        Tp[i * LDV + i] = beta;
+                        sm[QrSmem::TAU + i] = tau;
+                    }
+                }
+                __syncthreads();
+                const T tau = sm[QrSmem::TAU + i];
+                T d = T(0);
+#pragma unroll
+                for (int s2 = 0; s2 < RS; ++s2) d = fma(v[sub + 8 * s2], x[s2], d);
+                d = gsum(d);
+                if (j > i && j < bw) {
+                    const T sc = tau * (d + Tp[i * LDV + j]);
+#pragma unroll
+                    for (int s2 = 0; s2 < RS; ++s2) x[s2] = fma(-sc, v[sub + 8 * s2], x[s2]);
+                    if (sub == 0) Tp[i * LDV + j] -= sc;
+                }
+                T a = T(0);
+#pragma unroll
+                for (int s2 = 0; s2 < RS; ++s2) a = fma(x[s2], x[s2], a);
+                sig = gsum(a);
+            }
+#pragma unroll
+            for (int s2 = 0; s2 < RS; ++s2) {
+                const int r = sub + 8 * s2;
+                if (r < p) Vb[r * LDV + j] = x[s2];
             }
         }
         __syncthreads();
@@ -218,22 +547,57 @@ __device__ void tpqrt_wy(int n, int p, const Blk<T>& F, const Blk<T>* C, int nc,
         __syncthreads();
         // T factor (one warp; lane q keeps row q):  T[i][i] = tau_i,
         // T[0:i, i] = -tau_i T[0:i, 0:i] (V^T v_i).
+        // Lane q's row lives in Tm (only lane q reads it back), so the loop over i needs no
+        // register array indexed at run time; the loads of a step are independent of its sums.
         if (warp == 0) {
-            T row[PB];
-#pragma unroll
+            T* tq = Tm + lane * LDV;
             for (int i = 0; i < PB; ++i) {
-                T acc = T(0);
+                T a0 = T(0), a1 = T(0);
 #pragma unroll
-                for (int s = 0; s < PB; ++s)
-                    if (s < i && s >= lane) acc = fma(row[s], Y[s * LDV + i], acc);
+                for (int s = 0; s < PB; s += 2) {
+                    if (s < i && s >= lane) a0 = fma(tq[s], Y[s * LDV + i], a0);
+                    if (s + 1 < i && s + 1 >= lane) a1 = fma(tq[s + 1], Y[(s + 1) * LDV + i], a1);
+                }
                 const T ti = i < bw ? sm[QrSmem::TAU + i] : T(0);
-                row[i] = lane < i ? -ti * acc : (lane == i ? ti : T(0));
+                tq[i] = lane < i ? -ti * (a0 + a1) : (lane == i ? ti : T(0));
             }
-#pragma unroll
-            for (int i = 0; i < PB; ++i) Tm[lane * LDV + i] = row[i];
         }
         __syncthreads();
         // Trailing update: the rest of the factor, then every companion block.
+        if constexpr (sizeof(T) == 4) {
+            if (tc != nullptr) {
+                tc_panel_prep(p, bw, sm, *tc);
+                // Every trailing column (rest of the factor, then the companions) packed into
+                // chunks of TC_CW columns.
+                TcChunk ch;
+                ch.nseg = 0;
+                ch.w = 0;
+                auto flush = [&]() {
+                    if (ch.w > 0) {
+                        ch.off[ch.nseg] = ch.w;
+                        tc_apply_chunk(ch, kk0, bw, p, sm, *tc);
+                    }
+                    ch.nseg = 0;
+                    ch.w = 0;
+                };
+                auto add = [&](const Blk<T>& B, int first) {
+                    for (int c = first; c < B.ncols;) {
+                        if (ch.nseg == TC_SEGS || ch.w == TC_CW) flush();
+                        const int take = (B.ncols - c) < (TC_CW - ch.w) ? (B.ncols - c) : (TC_CW - ch.w);
+                        ch.b[ch.nseg] = B;
+                        ch.c0[ch.nseg] = c;
+                        ch.off[ch.nseg] = ch.w;
+                        ++ch.nseg;
+                        ch.w += take;
+                        c += take;
+                    }
+                };
+                add(F, kk0 + bw);
+                for (int b = 0; b < nc; ++b) add(C[b], 0);
+                flush();
+                continue;
+            }
+        }
         for (int c0 = kk0 + bw; c0 < n; c0 += CW)
             apply_chunk<T>(F, c0, (n - c0) < CW ? (n - c0) : CW, kk0, bw, p, sm);
         for (int b = 0; b < nc; ++b)
@@ -248,7 +612,7 @@ __device__ void tpqrt_wy(int n, int p, const Blk<T>& F, const Blk<T>* C, int nc,
 template <typename T>
 __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* out, T* R,
                            double* resid, const double* cn2, const double* cd2,
-                           unsigned long long* bad, T* sm) {
+                           unsigned long long* bad, T* sm, TcState* tc = nullptr) {
     const int tid = threadIdx.x;
     const int64_t nn = (int64_t)n * n;
     const int64_t CS = level_cs(n), RS = rstore_rs(n);
@@ -277,7 +641,7 @@ __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* ou
     {
         const Blk<T> F{Rj, n, rec_E(rs), 2 * n, n};
         const Blk<T> C[2] = {{Rj + 2 * nn, n, rec_E(rs) + n, 2 * n, n}, {Rj + 3 * nn, 1, rec_RE(rs), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 2, sm);
+        tpqrt_wy<T>(n, n, F, C, 2, sm, tc);
     }
     if (j >= 1) {
         // step 2: [Rtilde_j ; D_j], companions [0 ; -B_j] (left), [X_j ; 0] (right), [t_j ; rE_j];
@@ -293,7 +657,7 @@ __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* ou
         const Blk<T> C[3] = {{Rj + nn, n, rec_E(ro), 2 * n, n},
                              {Rj + 2 * nn, n, rec_E(ro) + n, 2 * n, n},
                              {Rj + 3 * nn, 1, rec_RE(ro), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 3, sm);
+        tpqrt_wy<T>(n, n, F, C, 3, sm, tc);
     }
     for (int c = tid; c < n; c += NTH)
         if (diag_is_singular<T>(Rj[(int64_t)c * n + c], cn2[oj * n + c] + cd2[oj * n + c], n))
@@ -317,7 +681,7 @@ __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* ou
         __syncthreads();
         const Blk<T> F{Re, n, rec_E(re) + n, 2 * n, n};
         const Blk<T> C[2] = {{Re + nn, n, rec_E(re), 2 * n, n}, {Re + 3 * nn, 1, rec_RE(re), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 2, sm);
+        tpqrt_wy<T>(n, n, F, C, 2, sm, tc);
         for (int c = tid; c < n; c += NTH)
             if (diag_is_singular<T>(Re[(int64_t)c * n + c], cn2[oe * n + c] + cd2[oe * n + c], n))
                 flag_error(bad, ST_SINGULAR, oe);
@@ -328,12 +692,12 @@ __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* ou
     {
         const Blk<T> F{rec_C(ro), n, rec_E(rs) + n, 2 * n, n};
         const Blk<T> C[1] = {{rec_RC(ro), 1, rec_RE(rs), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 1, sm);
+        tpqrt_wy<T>(n, n, F, C, 1, sm, tc);
     }
     if (triple) {
         const Blk<T> F{rec_C(ro), n, rec_E(re), 2 * n, n};
         const Blk<T> C[1] = {{rec_RC(ro), 1, rec_RE(re), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 1, sm);
+        tpqrt_wy<T>(n, n, F, C, 1, sm, tc);
     }
     if (threadIdx.x < 32) {
         double acc = 0.0;
@@ -443,7 +807,7 @@ __device__ void trsm_column_warp(const T* L, int d, T* X) {
 
 struct WhitenSmem {
     // FP64 packed factor, then its working-precision copy; the QR's buffers overlay both.
-    static size_t bytes(int n, bool fp32) {
+    __host__ __device__ static size_t bytes(int n, bool fp32) {
         const size_t tri = (size_t)n * (n + 1) / 2;
         size_t chol = tri * sizeof(double) + (fp32 ? tri * sizeof(float) : 0);
         chol = (chol + 15) & ~(size_t)15;
@@ -453,7 +817,7 @@ struct WhitenSmem {
 };
 
 template <typename T>
-__device__ void whiten_step(const WhitenArgs& a, int64_t i, unsigned char* smem) {
+__device__ void whiten_step(const WhitenArgs& a, int64_t i, unsigned char* smem, TcState* tc = nullptr) {
     const int n = a.n, tid = threadIdx.x;
     const int64_t nn = (int64_t)n * n, CS = level_cs(n);
     double* Lpk = reinterpret_cast<double*>(smem);
@@ -543,7 +907,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, unsigned char* smem)
         // [Chat_i | rC_i] = R of [0 ; L_C^{-1} [G_i | o_i]]
         const Blk<T> F{rec, n, Gm, n + 1, n};
         const Blk<T> C[1] = {{rec + nn, 1, Gm + n, n + 1, 1}};
-        tpqrt_wy<T>(n, mi, F, C, 1, reinterpret_cast<T*>(smem));
+        tpqrt_wy<T>(n, mi, F, C, 1, reinterpret_cast<T*>(smem), tc);
     }
     if (tid < 32) {
         double acc = 0.0;
@@ -722,19 +1086,35 @@ __device__ void selinv_row(int n, int64_t k, int level, int64_t q, const T* __re
 }
 
 // ------------------------------------------------------------------------------------------
+// tc_off >= 0 (FP32 only): byte offset of the tensor-core region in shared memory; the block
+// then holds TMEM for its whole life.  tc_off < 0: CUDA-core trailing updates.
 template <typename T>
-__global__ void __launch_bounds__(NTH) whiten_k(WhitenArgs a) {
+__global__ void __launch_bounds__(NTH) whiten_k(WhitenArgs a, int tc_off) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    for (int64_t i = blockIdx.x; i < a.k; i += gridDim.x) whiten_step<T>(a, i, smem_raw);
+    TcState tcs;
+    TcState* tc = nullptr;
+    if (sizeof(T) == 4 && tc_off >= 0) {
+        tc_setup(tcs, smem_raw + tc_off, a.bad);
+        tc = &tcs;
+    }
+    for (int64_t i = blockIdx.x; i < a.k; i += gridDim.x) whiten_step<T>(a, i, smem_raw, tc);
+    if (tc != nullptr) tc_teardown(tcs);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(NTH) level_k(int n, int64_t nc, int level, T* in, T* out, T* R,
                                                double* resid, const double* cn2, const double* cd2,
-                                               unsigned long long* bad) {
+                                               unsigned long long* bad, int tc_off) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    TcState tcs;
+    TcState* tc = nullptr;
+    if (sizeof(T) == 4 && tc_off >= 0) {
+        tc_setup(tcs, smem_raw + tc_off, bad);
+        tc = &tcs;
+    }
     for (int64_t t = blockIdx.x; t < nc / 2; t += gridDim.x)
-        level_tile<T>(n, nc, level, t, in, out, R, resid, cn2, cd2, bad, reinterpret_cast<T*>(smem_raw));
+        level_tile<T>(n, nc, level, t, in, out, R, resid, cn2, cd2, bad, reinterpret_cast<T*>(smem_raw), tc);
+    if (tc != nullptr) tc_teardown(tcs);
 }
 
 template <typename T>
@@ -747,26 +1127,34 @@ __global__ void __launch_bounds__(NTH) selinv_k(int n, int64_t k, int level, con
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(NTH) batch_k(const BatchWork* wk) {
+__global__ void __launch_bounds__(NTH) batch_k(const BatchWork* wk, int tc_off) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const BatchWork w = *wk;
     const int64_t total = w.off[w.np];
+    TcState tcs;
+    TcState* tc = nullptr;
+    if (sizeof(T) == 4 && OP != B_SELINV && tc_off >= 0) {
+        tc_setup(tcs, smem_raw + tc_off, w.np > 0 ? w.desc[w.probs[0]].bad : nullptr);
+        tc = &tcs;
+    }
     for (int64_t u = blockIdx.x; u < total; u += gridDim.x) {
         const int pi = batch_find(w.off, w.np, u);
         const ProbDesc& P = w.desc[w.probs[pi]];
         const int64_t x = u - w.off[pi];
         const int l = work_level(w, P);
+        if (tc != nullptr) tc->bad = P.bad;
         if constexpr (OP == B_WHITEN) {
-            whiten_step<T>(whiten_args_of(P), x, smem_raw);
+            whiten_step<T>(whiten_args_of(P), x, smem_raw, tc);
         } else if constexpr (OP == B_LEVEL) {
             level_tile<T>(P.n, P.k >> l, l, x, reinterpret_cast<T*>(P.lvl[l & 1]),
                           reinterpret_cast<T*>(P.lvl[(l + 1) & 1]), reinterpret_cast<T*>(P.R), P.resid,
-                          P.cn2, P.cd2, P.bad, reinterpret_cast<T*>(smem_raw));
+                          P.cn2, P.cd2, P.bad, reinterpret_cast<T*>(smem_raw), tc);
         } else {
             selinv_row<T>(P.n, P.k, l, x, reinterpret_cast<const T*>(P.R), reinterpret_cast<T*>(P.Sx),
                           P.cov, P.bad, reinterpret_cast<T*>(smem_raw));
         }
     }
+    if (tc != nullptr) tc_teardown(tcs);
 }
 
 unsigned grid_of(int64_t units, int per_sm) {
@@ -788,6 +1176,22 @@ void set_smem(K kern, size_t bytes) {
 
 size_t qr_bytes(bool fp32) { return (size_t)QrSmem::TOTAL * (fp32 ? sizeof(float) : sizeof(double)); }
 
+// Whether the FP32 kernels use the tensor cores (KS_NO_TC=1 selects the CUDA-core updates).
+bool tc_enabled() {
+    const char* v = getenv("KS_NO_TC");
+    return !(v && *v && *v != '0');
+}
+// Shared memory of an FP32 kernel whose own layout takes `base` bytes: the tensor-core region
+// follows at tc_align(base); *off receives that offset (-1 without tensor cores).
+size_t with_tc(size_t base, bool fp32, int* off) {
+    if (!fp32 || !tc_enabled()) {
+        *off = -1;
+        return base;
+    }
+    *off = (int)tc_align(base);
+    return tc_align(base) + TcSmem::BYTES;
+}
+
 }  // namespace large
 
 size_t large_smem_bytes(int n, bool fp32) {
@@ -800,14 +1204,15 @@ size_t large_smem_bytes(int n, bool fp32) {
 
 cudaError_t launch_whiten_large(const WhitenArgs& a, bool fp32, cudaStream_t st) {
     using namespace large;
-    const size_t smem = WhitenSmem::bytes(a.n, fp32);
-    const unsigned grid = grid_of(a.k, 2);
+    int tc_off = -1;
+    const size_t smem = with_tc(WhitenSmem::bytes(a.n, fp32), fp32, &tc_off);
+    const unsigned grid = grid_of(a.k, tc_off >= 0 ? 1 : 2);
     if (fp32) {
         set_smem(whiten_k<float>, smem);
-        whiten_k<float><<<grid, NTH, smem, st>>>(a);
+        whiten_k<float><<<grid, NTH, smem, st>>>(a, tc_off);
     } else {
         set_smem(whiten_k<double>, smem);
-        whiten_k<double><<<grid, NTH, smem, st>>>(a);
+        whiten_k<double><<<grid, NTH, smem, st>>>(a, -1);
     }
     ++t_launches;
     return cudaGetLastError();
@@ -818,14 +1223,15 @@ cudaError_t launch_level_large(int n, int64_t nc, int level, void* in, void* out
                                unsigned long long* bad, bool fp32, cudaStream_t st) {
     using namespace large;
     if (nc < 2) return cudaSuccess;
-    const size_t smem = qr_bytes(fp32);
-    const unsigned grid = grid_of(nc / 2, 2);
+    int tc_off = -1;
+    const size_t smem = with_tc(qr_bytes(fp32), fp32, &tc_off);
+    const unsigned grid = grid_of(nc / 2, tc_off >= 0 ? 1 : 2);
     if (fp32) {
         set_smem(level_k<float>, smem);
-        level_k<float><<<grid, NTH, smem, st>>>(n, nc, level, (float*)in, (float*)out, (float*)R, resid, cn2, cd2, bad);
+        level_k<float><<<grid, NTH, smem, st>>>(n, nc, level, (float*)in, (float*)out, (float*)R, resid, cn2, cd2, bad, tc_off);
     } else {
         set_smem(level_k<double>, smem);
-        level_k<double><<<grid, NTH, smem, st>>>(n, nc, level, (double*)in, (double*)out, (double*)R, resid, cn2, cd2, bad);
+        level_k<double><<<grid, NTH, smem, st>>>(n, nc, level, (double*)in, (double*)out, (double*)R, resid, cn2, cd2, bad, -1);
     }
     ++t_launches;
     return cudaGetLastError();
@@ -853,14 +1259,19 @@ cudaError_t launch_batch_large(int op, int n, const BatchWork* wk, bool fp32, un
                                cudaStream_t st) {
     using namespace large;
     size_t smem = 0;
-    if (op == B_WHITEN) smem = WhitenSmem::bytes(n, fp32);
-    else if (op == B_LEVEL) smem = qr_bytes(fp32);
+    int tc_off = -1;
+    if (op == B_WHITEN) smem = with_tc(WhitenSmem::bytes(n, fp32), fp32, &tc_off);
+    else if (op == B_LEVEL) smem = with_tc(qr_bytes(fp32), fp32, &tc_off);
     else if (op == B_SELINV) smem = SelSmem::bytes(n, fp32);
     else return cudaErrorInvalidValue;
-#define KS_LARGE_BATCH(TT, OPV)                       \
-    do {                                              \
-        set_smem(batch_k<TT, OPV>, smem);             \
-        batch_k<TT, OPV><<<grid, NTH, smem, st>>>(wk); \
+    if (tc_off >= 0) {   // one block per SM holds the whole TMEM
+        const unsigned one = grid_of(1LL << 40, 1);
+        if (grid > one) grid = one;
+    }
+#define KS_LARGE_BATCH(TT, OPV)                               \
+    do {                                                      \
+        set_smem(batch_k<TT, OPV>, smem);                     \
+        batch_k<TT, OPV><<<grid, NTH, smem, st>>>(wk, tc_off); \
     } while (0)
     if (fp32) {
         if (op == B_WHITEN) KS_LARGE_BATCH(float, B_WHITEN);

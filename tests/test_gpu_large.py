@@ -3,6 +3,8 @@ oracle, through the C ABI: states, covariances and residual, on lengths whose le
 widths (the three-block tail of Section 3), ragged observation counts, the error report of a
 non-SPD covariance, a batch mixing large and small problems, and a served request.
 Tolerances as in the other parity tests (FP64 1e-10; FP32 + refinement states 1e-6).
+In FP32 the trailing updates of the blocked QRs run on the tensor cores (3xTF32); KS_NO_TC=1
+selects the CUDA-core updates, and both must agree with the oracle and with each other.
 """
 import numpy as np
 import pytest
@@ -47,6 +49,25 @@ def test_large_matches_oracle(n, k, precision):
     else:
         assert rel(u, ref["u"]) < 1e-6
         assert rel_blocks(cov, ref["cov"]) < 1e-3
+
+
+@pytest.mark.parametrize("n,k,m", [(72, 13, 72), (128, 9, 128), (100, 16, 61)])
+def test_large_tensor_core_updates_match_cuda_cores(n, k, m, monkeypatch):
+    """Chunks of 16..128 columns (and narrower ones left to the CUDA cores), depths p = n and
+    p = m < n (the whitening QR), levels of odd width."""
+    p = inputs.random_problem(k, n, m, seed=900 + n, with_c=True, f_scale=0.99)
+    ref = oracle.smooth(p)
+    out = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("KS_NO_TC", flag)
+        with Smoother(device=0, precision="fp32_refine") as sm:
+            out[flag] = run(sm, p)
+    for flag in ("0", "1"):
+        u, cov, _ = out[flag]
+        assert rel(u, ref["u"]) < 1e-6, flag
+        assert rel_blocks(cov, ref["cov"]) < 1e-3, flag
+    assert rel(out["0"][0], out["1"][0]) < 1e-6
+    assert rel_blocks(out["0"][1], out["1"][1]) < 1e-3
 
 
 def test_large_ragged_observations():
