@@ -721,18 +721,23 @@ __device__ __forceinline__ int tri_(int r) { return r * (r + 1) / 2; }
 
 // Lower Cholesky factor of the d x d matrix held packed (row-major lower) in L, FP64, all
 // threads.  A non-positive or non-finite pivot flags ST_NOT_SPD at `step` and is replaced by 1.
+// The pivot's square root and reciprocal and the column scaling are done by warp 0 alone: an
+// FP64 warp instruction occupies the FP64 pipe whatever its active lanes, so the other warps
+// would only repeat them.
 __device__ void chol_packed(double* L, int d, unsigned long long* bad, int64_t step) {
     const int tid = threadIdx.x;
-    for (int j = 0; j < d; ++j) {
-        double ajj = L[tri_(j) + j];
-        if (!(ajj > 0.0) || !isfinite(ajj)) {
-            if (tid == 0) flag_error(bad, ST_NOT_SPD, step);
-            ajj = 1.0;
+    for (int j = 0; j < d; ++j) {   // the caller synchronises after filling L
+        if (tid < 32) {
+            double ajj = L[tri_(j) + j];
+            if (!(ajj > 0.0) || !isfinite(ajj)) {
+                if (tid == 0) flag_error(bad, ST_NOT_SPD, step);
+                ajj = 1.0;
+            }
+            const double dj = sqrt(ajj), inv = 1.0 / dj;
+            __syncwarp();
+            if (tid == 0) L[tri_(j) + j] = dj;
+            for (int r = j + 1 + tid; r < d; r += 32) L[tri_(r) + j] *= inv;
         }
-        const double dj = sqrt(ajj), inv = 1.0 / dj;
-        __syncthreads();
-        if (tid == 0) L[tri_(j) + j] = dj;
-        for (int r = j + 1 + tid; r < d; r += NTH) L[tri_(r) + j] *= inv;
         __syncthreads();
         const int t = d - j - 1;
         const int cnt = t * (t + 1) / 2;
