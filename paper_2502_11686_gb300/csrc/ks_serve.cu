@@ -442,22 +442,20 @@ void scheduler(ks_server* S) {
         };
         S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || schedulable() || !S->inflight.empty(); });
         if (S->stop && S->queue.empty() && S->active.empty() && S->inflight.empty()) break;
-        // admission in arrival order
-        while (!S->queue.empty()) {
-            Req* r = S->queue.front();
-            const size_t need = plan_request(S, r, false);
-            const size_t budget = S->opt.mem_budget;
-            if (need > budget) {
-                S->queue.pop_front();
-                r->status = KS_ERR_OOM;
-                r->state = 3;
-                r->t_done = Clock::now();
-                S->n_completed++;
-                S->cv_done.notify_all();
-                continue;
-            }
-            if ((int)S->active.size() >= S->opt.max_active || S->used + need > budget) break;
-            S->queue.pop_front();
+        // Admission.  Covariance follow-ups go first, from any queue position: they run on a
+        // factor that is already resident, and the caller may hold that factor (and its memory)
+        // until the follow-up is done, so a follow-up waiting behind a new request that needs
+        // that memory would never be admitted.  New requests then go in arrival order.
+        auto fail_oom = [&](Req* r) {
+            r->status = KS_ERR_OOM;
+            r->state = 3;
+            r->t_done = Clock::now();
+            S->n_completed++;
+            S->cv_done.notify_all();
+        };
+        // Allocates and plans r (removed from the queue by the caller); 0 admitted, 1 no memory
+        // now (r not admitted), 2 rejected with KS_ERR_OOM.
+        auto admit = [&](Req* r, size_t need) -> int {
             lk.unlock();
             void* p = nullptr;
             const cudaError_t e = cudaMallocAsync(&p, need, S->st);
@@ -465,15 +463,10 @@ void scheduler(ks_server* S) {
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 if (S->active.empty() && S->inflight.empty()) {   // nothing will free memory
-                    r->status = KS_ERR_OOM;
-                    r->state = 3;
-                    r->t_done = Clock::now();
-                    S->n_completed++;
-                    S->cv_done.notify_all();
-                    continue;
+                    fail_oom(r);
+                    return 2;
                 }
-                S->queue.push_front(r);
-                break;
+                return 1;
             }
             r->arena = p;
             r->bytes = need;
@@ -487,6 +480,47 @@ void scheduler(ks_server* S) {
             r->t_admit = Clock::now();
             S->n_admitted++;
             S->active.push_back(r);
+            return 0;
+        };
+        const size_t budget = S->opt.mem_budget;
+        for (auto it = S->queue.begin(); it != S->queue.end();) {
+            Req* r = *it;
+            if (r->follow_of < 0) {
+                ++it;
+                continue;
+            }
+            const size_t need = plan_request(S, r, false);
+            if (need > budget) {
+                it = S->queue.erase(it);
+                fail_oom(r);
+                continue;
+            }
+            if ((int)S->active.size() >= S->opt.max_active || S->used + need > budget) {
+                ++it;
+                continue;
+            }
+            const size_t pos = (size_t)(it - S->queue.begin());
+            S->queue.erase(it);
+            if (admit(r, need) == 1) {
+                S->queue.insert(S->queue.begin() + pos, r);
+                break;
+            }
+            it = S->queue.begin() + pos;
+        }
+        while (!S->queue.empty()) {
+            Req* r = S->queue.front();
+            const size_t need = plan_request(S, r, false);
+            if (need > budget) {
+                S->queue.pop_front();
+                fail_oom(r);
+                continue;
+            }
+            if ((int)S->active.size() >= S->opt.max_active || S->used + need > budget) break;
+            S->queue.pop_front();
+            if (admit(r, need) == 1) {
+                S->queue.push_front(r);
+                break;
+            }
         }
         std::vector<Req*> sched;
         for (Req* r : S->active)

@@ -132,6 +132,44 @@ def test_admission_waits_for_memory():
     assert binfo["status"] == native.KS_ERR_OOM   # larger than the whole budget
 
 
+def test_follow_up_not_blocked_by_a_waiting_request():
+    """A covariance follow-up is admitted ahead of an earlier request that waits for memory held
+    by the follow-up's own kept factor (admitting in arrival order alone would wait forever)."""
+    pa = inputs.random_problem(3000, 6, 6, seed=61)
+    pb = inputs.random_problem(4500, 6, 6, seed=62)
+    with Smoother(device=0, precision="fp64") as sm:
+        ua_ref, cov_ref = alone(sm, pa, True)
+        ub_ref = alone(sm, pb, False)[0]
+        probe = native.ks_server_create(sm.ctx, keep_factors=True)
+        sizes = []
+        for p in (pa, pb):
+            rid = native.ks_server_submit(probe, request(p, False))
+            assert native.ks_server_wait(probe, rid, 60_000.0)["status"] == native.KS_OK
+            sizes.append(native.ks_server_stats(probe)["bytes_in_use"])
+            native.ks_server_release(probe, rid)
+        native.ks_server_destroy(probe)
+        a, b = sizes
+        budget = 2 * a + (1 << 19)
+        assert b <= budget < a + b
+        srv = native.ks_server_create(sm.ctx, mem_budget=budget, keep_factors=True)
+        ra, rb = request(pa, False), request(pb, False)
+        ida = native.ks_server_submit(srv, ra)
+        assert native.ks_server_wait(srv, ida, 60_000.0)["status"] == native.KS_OK
+        idb = native.ks_server_submit(srv, rb)            # waits: A's factor holds the memory
+        cov = np.zeros((pa.k, pa.n, pa.n))
+        fid = native.ks_server_covariances(srv, ida, cov)  # queued after B
+        finfo = native.ks_server_wait(srv, fid, 60_000.0)
+        assert finfo["done"] and finfo["status"] == native.KS_OK
+        assert native.ks_server_release(srv, fid) == native.KS_OK
+        assert native.ks_server_release(srv, ida) == native.KS_OK
+        binfo = native.ks_server_wait(srv, idb, 60_000.0)
+        native.ks_server_destroy(srv)
+    assert binfo["done"] and binfo["status"] == native.KS_OK
+    assert rel_blocks(cov, cov_ref) < 1e-10
+    assert rel(ra["u_out"].cpu().numpy(), ua_ref) < 1e-10
+    assert rel(rb["u_out"].cpu().numpy(), ub_ref) < 1e-10
+
+
 def generated(ctx, k, n, m, seed):
     import torch
     dev = "cuda"
