@@ -739,15 +739,18 @@ __device__ void chol_packed(double* L, int d, unsigned long long* bad, int64_t s
             for (int r = j + 1 + tid; r < d; r += 32) L[tri_(r) + j] *= inv;
         }
         __syncthreads();
+        // Trailing update: row r of the triangle by warp (r - j - 1) % 8, its columns by the
+        // lanes (no index decoding; rows shorter than a warp leave lanes idle).
         const int t = d - j - 1;
-        const int cnt = t * (t + 1) / 2;
-        for (int e = tid; e < cnt; e += NTH) {
-            int rr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-            while (tri_(rr + 1) <= e) ++rr;
-            while (tri_(rr) > e) --rr;
-            const int cc = e - tri_(rr);
-            const int r = j + 1 + rr, c = j + 1 + cc;
-            L[tri_(r) + c] = fma(-L[tri_(r) + j], L[tri_(c) + j], L[tri_(r) + c]);
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int rr = warp; rr < t; rr += NTH / 32) {
+            const int r = j + 1 + rr;
+            double* Lr = L + tri_(r);
+            const double lrj = Lr[j];
+            for (int cc = lane; cc <= rr; cc += 32) {
+                const int c = j + 1 + cc;
+                Lr[c] = fma(-lrj, L[tri_(c) + j], Lr[c]);
+            }
         }
         __syncthreads();
     }
@@ -761,6 +764,8 @@ __device__ void trsm_column(const T* L, int d, T* X, int64_t ldx) {
         T acc[32];
 #pragma unroll
         for (int ii = 0; ii < 32; ++ii) acc[ii] = (rb + ii < d) ? X[(int64_t)(rb + ii) * ldx] : T(0);
+        // Unrolled so that the loads of the solved values (device memory) are issued in batches.
+#pragma unroll 8
         for (int q = 0; q < rb; ++q) {
             const T xq = X[(int64_t)q * ldx];
 #pragma unroll
