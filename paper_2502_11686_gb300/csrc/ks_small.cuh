@@ -156,6 +156,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
 #pragma unroll
             for (int c = 0; c <= r; ++c) L[r][c] = Ki[r * N + c];
         bool bad = false;
+        double linv[N];   // 1 / diag(L), reused by the solves (an FP64 divide is costly)
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             double dj = L[j][j];
@@ -165,6 +166,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
             dj = (dj > 0.0 && isfinite(dj)) ? sqrt(dj) : 1.0;
             L[j][j] = dj;
             const double inv = 1.0 / dj;
+            linv[j] = inv;
 #pragma unroll
             for (int r = j + 1; r < N; ++r) {
                 double s = L[r][j];
@@ -184,7 +186,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
         T Lt[N][N], dinv[N];
 #pragma unroll
         for (int r = 0; r < N; ++r) {
-            dinv[r] = T(1) / (T)L[r][r];
+            dinv[r] = (T)linv[r];
 #pragma unroll
             for (int c = 0; c < r; ++c) Lt[r][c] = (T)L[r][c];
         }
@@ -252,6 +254,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
             for (int c = 0; c <= r; ++c)
                 Lo[r][c] = (r < mi) ? Ci[r * mi + c] : (r == c ? 1.0 : 0.0);
         bool bad = false;
+        double oinv[N];   // 1 / diag(Lo), reused by the solve
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             double dj = Lo[j][j];
@@ -261,6 +264,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
             dj = (dj > 0.0 && isfinite(dj)) ? sqrt(dj) : 1.0;
             Lo[j][j] = dj;
             const double inv = 1.0 / dj;
+            oinv[j] = inv;
 #pragma unroll
             for (int r = j + 1; r < N; ++r) {
                 double s = Lo[r][j];
@@ -288,7 +292,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, T* out0) {
         }
 #pragma unroll
         for (int r = 0; r < N; ++r) {
-            const T dv = T(1) / (T)Lo[r][r];
+            const T dv = (T)oinv[r];
 #pragma unroll
             for (int p = 0; p < r; ++p) {
                 const T l = (T)Lo[r][p];
