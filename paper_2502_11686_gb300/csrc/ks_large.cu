@@ -719,37 +719,51 @@ __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* ou
 // Whitening of step i.
 __device__ __forceinline__ int tri_(int r) { return r * (r + 1) / 2; }
 
+// Pivot j of the packed factor L by one warp: square root and reciprocal of L_jj, then column j
+// scaled.  A non-positive or non-finite pivot flags ST_NOT_SPD at `step` and is replaced by 1.
+__device__ __forceinline__ void chol_pivot_warp(double* L, int d, int j, int lane,
+                                                unsigned long long* bad, int64_t step) {
+    double ajj = L[tri_(j) + j];
+    if (!(ajj > 0.0) || !isfinite(ajj)) {
+        if (lane == 0) flag_error(bad, ST_NOT_SPD, step);
+        ajj = 1.0;
+    }
+    const double dj = sqrt(ajj), inv = 1.0 / dj;
+    __syncwarp();
+    if (lane == 0) L[tri_(j) + j] = dj;
+    for (int r = j + 1 + lane; r < d; r += 32) L[tri_(r) + j] *= inv;
+    __syncwarp();
+}
+
 // Lower Cholesky factor of the d x d matrix held packed (row-major lower) in L, FP64, all
-// threads.  A non-positive or non-finite pivot flags ST_NOT_SPD at `step` and is replaced by 1.
-// The pivot's square root and reciprocal and the column scaling are done by warp 0 alone: an
-// FP64 warp instruction occupies the FP64 pipe whatever its active lanes, so the other warps
-// would only repeat them.
+// threads, right-looking with look-ahead: during step j warp 0 updates column j+1 alone, takes
+// pivot j+1 and scales that column, while warps 1-7 update the columns >= j+2 of the trailing
+// triangle (row r by warp 1 + (r - j - 2) % 7, its columns by the lanes).  One barrier per pivot,
+// and the pivot's latency overlaps the trailing update.  Warp 0 alone does the square root and
+// reciprocal: an FP64 warp instruction occupies the FP64 pipe whatever its active lanes.  The
+// caller synchronises after filling L.
 __device__ void chol_packed(double* L, int d, unsigned long long* bad, int64_t step) {
-    const int tid = threadIdx.x;
-    for (int j = 0; j < d; ++j) {   // the caller synchronises after filling L
-        if (tid < 32) {
-            double ajj = L[tri_(j) + j];
-            if (!(ajj > 0.0) || !isfinite(ajj)) {
-                if (tid == 0) flag_error(bad, ST_NOT_SPD, step);
-                ajj = 1.0;
-            }
-            const double dj = sqrt(ajj), inv = 1.0 / dj;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int NW = NTH / 32;
+    if (warp == 0) chol_pivot_warp(L, d, 0, lane, bad, step);
+    __syncthreads();
+    for (int j = 0; j + 1 < d; ++j) {
+        if (warp == 0) {
+            const double l1 = L[tri_(j + 1) + j];
+            for (int r = j + 1 + lane; r < d; r += 32)
+                L[tri_(r) + j + 1] = fma(-L[tri_(r) + j], l1, L[tri_(r) + j + 1]);
             __syncwarp();
-            if (tid == 0) L[tri_(j) + j] = dj;
-            for (int r = j + 1 + tid; r < d; r += 32) L[tri_(r) + j] *= inv;
-        }
-        __syncthreads();
-        // Trailing update: row r of the triangle by warp (r - j - 1) % 8, its columns by the
-        // lanes (no index decoding; rows shorter than a warp leave lanes idle).
-        const int t = d - j - 1;
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int rr = warp; rr < t; rr += NTH / 32) {
-            const int r = j + 1 + rr;
-            double* Lr = L + tri_(r);
-            const double lrj = Lr[j];
-            for (int cc = lane; cc <= rr; cc += 32) {
-                const int c = j + 1 + cc;
-                Lr[c] = fma(-lrj, L[tri_(c) + j], Lr[c]);
+            chol_pivot_warp(L, d, j + 1, lane, bad, step);
+        } else {
+            const int t = d - j - 2;
+            for (int rr = warp - 1; rr < t; rr += NW - 1) {
+                const int r = j + 2 + rr;
+                double* Lr = L + tri_(r);
+                const double lrj = Lr[j];
+                for (int cc = lane; cc <= rr; cc += 32) {
+                    const int c = j + 2 + cc;
+                    Lr[c] = fma(-lrj, L[tri_(c) + j], Lr[c]);
+                }
             }
         }
         __syncthreads();
