@@ -1218,10 +1218,14 @@ size_t with_tc(size_t base, bool fp32, int* off) {
 
 }  // namespace large
 
+// Largest dynamic shared memory a large-state launch of this n requests (with the tensor-core
+// region of the FP32 whitening and level kernels).
 size_t large_smem_bytes(int n, bool fp32) {
     using namespace large;
-    size_t m = WhitenSmem::bytes(n, fp32);
-    if (qr_bytes(fp32) > m) m = qr_bytes(fp32);
+    int off = -1;
+    size_t m = with_tc(WhitenSmem::bytes(n, fp32), fp32, &off);
+    const size_t q = with_tc(qr_bytes(fp32), fp32, &off);
+    if (q > m) m = q;
     if (SelSmem::bytes(n, fp32) > m) m = SelSmem::bytes(n, fp32);
     return m;
 }
