@@ -1,5 +1,5 @@
 // fma_probe.cu -- FMA issue rates of the GPU: DFMA and FFMA, full vs partially active warps,
-// warps per SM.  Sets the FP64 / FP32 denominators the kernels are judged against.
+// warps per SM.  Gives the FP64 / FP32 rates the kernels are measured against.
 // Build and run: python -m paper_2502_11686_gb300.probes
 #include <cstdio>
 #include <cuda_runtime.h>
