@@ -459,9 +459,11 @@ def main():
     ap.add_argument("--workload", default="long_k1e6_n6",
                     choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + ["serve"])
     ap.add_argument("--nprob", type=int, default=None, help="batched workloads: problem count")
-    ap.add_argument("--rates", default="25,50,100,200,400,800,2000",
-                    help="serve workload: offered request rates (req/s) to sweep")
-    ap.add_argument("--duration", type=float, default=6.0, help="serve workload: seconds per rate")
+    ap.add_argument("--rates", default="25,100,400,2000",
+                    help="serve workload: offered request rates (req/s) to sweep, ascending; the "
+                         "sweep stops at the first saturated rate")
+    ap.add_argument("--duration", type=float, default=3.0,
+                    help="serve workload: seconds of arrivals per rate (each rate then drains)")
     ap.add_argument("--serve-n", default="6,24,48,128", help="serve workload: state sizes")
     ap.add_argument("--max-queue", type=int, default=32,
                     help="serve workload: a rate whose admission queue exceeds this is saturated")
