@@ -61,8 +61,14 @@ typedef enum {
                               not determined by the data); info = state index */
     KS_ERR_OOM = 4,        /* device allocation failed */
     KS_ERR_CUDA = 5,       /* a CUDA runtime call failed; see ks_last_error */
-    KS_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
-    KS_ERR_NO_FACTOR = 7   /* the handle holds no factorization */
+    KS_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up (the tensor-core completion
+                              waits of the FP32 large-state kernels, about a second each); the
+                              call's outputs are undefined, the ctx stays usable */
+    KS_ERR_NO_FACTOR = 7,  /* the handle holds no factorization */
+    KS_ERR_NONFINITE = 8   /* ks_smooth: an input value that enters the equations of state i is
+                              NaN or infinite (F_i, c_i, G_i, o_i, or H_{i-1}, which multiplies
+                              u_i); info = i.  A non-finite K_i or C_i has no Cholesky factor and
+                              gives KS_ERR_NOT_SPD instead */
 } ks_status;
 
 typedef enum {
@@ -202,6 +208,8 @@ typedef struct {
     int64_t submitted, admitted, completed, active, queued;
     int64_t ticks, launches;
     size_t bytes_in_use, bytes_budget;
+    int64_t shared_launches;          /* launches that carried the work of two or more requests */
+    int64_t max_requests_per_launch;  /* most requests that one launch carried */
 } ks_server_counters;
 
 ks_status ks_server_create(ks_ctx *ctx, const ks_server_options *opt, ks_server **out);
@@ -286,6 +294,12 @@ ks_status ks_smooth_static(int device, void *stream, int64_t k, int n, int m,
                            const double *G, const double *o, const double *C,
                            double *u_out, double *cov_out, int64_t *info,
                            char *err, size_t err_len);
+
+/* Measures the FMA rate of `device` in TFLOP/s (an FMA is two flops): FP64 for KS_FP64, FP32 for
+ * KS_FP32_REFINE.  A measurement aid for rooflines (the paper has no counterpart): the
+ * arithmetic-bound kernels are compared against this rate.  Runs two short kernels (about 30 ms)
+ * on a private stream and allocates 16 bytes.  Returns KS_OK, KS_ERR_ARG or KS_ERR_CUDA. */
+ks_status ks_measure_fma_rate(int device, int precision, double *tflops);
 
 /* Largest state dimension n this ctx's precision supports on its device (128 on GB300: up to
  * 48 (FP64) / 64 (FP32) with shared-memory tiles, above that with the large-state kernels, which

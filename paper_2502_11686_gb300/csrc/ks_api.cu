@@ -269,6 +269,7 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     {
         Phase ph(ctx, KS_PHASE_WHITEN);
         KS_CUDA(ctx, sops ? sops->whiten(wa, fp32, st) : launch_whiten(wa, fp32, st));
+        KS_CUDA(ctx, launch_check_finite(wa, st));
     }
 
     // Odd-even levels.

@@ -495,11 +495,10 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
                                  cudaMemcpyDeviceToHost, st));
     KS_CUDA(ctx, cudaStreamSynchronize(st));
     ks_status first = KS_OK;
-    static const int order[] = {ST_NOT_SPD, ST_SINGULAR, ST_TIMEOUT, ST_ARG};
     for (int p = 0; p < nprob; ++p) {
         int sp = KS_OK;
         int64_t ip = -1;
-        for (int code : order)
+        for (int code : status_order)
             if (words[(size_t)p * ST_NCODES + code] != ~0ULL) {
                 sp = code;
                 ip = (int64_t)words[(size_t)p * ST_NCODES + code];

@@ -155,15 +155,10 @@ inline ks_status collect_status(ks_ctx* ctx, int64_t* info) {
                                  cudaMemcpyDeviceToHost, ctx->stream));
     KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     KS_CUDA(ctx, cudaMemsetAsync(ctx->d_bad, 0xFF, sizeof(unsigned long long) * ST_NCODES, ctx->stream));
-    static const int order[] = {ST_NOT_SPD, ST_SINGULAR, ST_TIMEOUT, ST_ARG};
-    for (int code : order) {
+    for (int code : status_order) {
         if (ctx->h_bad[code] != ~0ULL) {
             if (info) *info = (int64_t)ctx->h_bad[code];
-            const char* what = code == ST_NOT_SPD ? "a covariance matrix is not SPD at step"
-                               : code == ST_SINGULAR ? "singular diagonal block of R at state"
-                               : code == ST_TIMEOUT ? "device wait timed out at"
-                                                    : "bad argument detected on device at";
-            return fail(ctx, (ks_status)code, "%s %lld", what, (long long)ctx->h_bad[code]);
+            return fail(ctx, (ks_status)code, "%s %lld", status_message(code), (long long)ctx->h_bad[code]);
         }
     }
     if (info) *info = -1;

@@ -20,7 +20,22 @@
 
 namespace ks {
 
-enum { ST_ARG = 1, ST_NOT_SPD = 2, ST_SINGULAR = 3, ST_TIMEOUT = 6, ST_NCODES = 8 };
+enum { ST_ARG = 1, ST_NOT_SPD = 2, ST_SINGULAR = 3, ST_TIMEOUT = 6, ST_NONFINITE = 8, ST_NCODES = 9 };
+
+// Order in which a call reports its device error words (the first one set wins), and the
+// message of each.  A non-finite input, or a timed-out wait (which leaves the rest of that
+// launch's results undefined), makes R look singular as well, so both are reported first.
+constexpr int status_order[] = {ST_NOT_SPD, ST_NONFINITE, ST_TIMEOUT, ST_SINGULAR, ST_ARG};
+inline const char* status_message(int code) {
+    switch (code) {
+        case ST_NOT_SPD: return "a covariance matrix is not SPD at step";
+        case ST_NONFINITE: return "a non-finite input value (NaN or Inf) in the equations of state";
+        case ST_SINGULAR: return "singular diagonal block of R at state";
+        case ST_TIMEOUT: return "a bounded device wait gave up (tensor-core completion) at";
+        case ST_ARG: return "bad argument detected on device at";
+        default: return "device error at";
+    }
+}
 
 // Device error words: bad[code] = smallest failing index seen (ULLONG_MAX = none).
 __device__ __forceinline__ void flag_error(unsigned long long* bad, int code, long long idx) {
@@ -230,6 +245,11 @@ __device__ __forceinline__ bool diag_is_singular(T d, double colnorm2, int n) {
 }
 
 cudaError_t launch_whiten(const WhitenArgs& a, bool fp32, cudaStream_t st);
+
+// After the whitening: flags ST_NONFINITE at state i when a column norm of the whitened blocks
+// of state i (cn2, cd2: F_i, H_{i-1}, G_i through the whitening) or an entry of o_i or c_i is
+// NaN or infinite.  Grid-stride and coalesced over each array.
+cudaError_t launch_check_finite(const WhitenArgs& a, cudaStream_t st);
 
 // Large-state path (one thread block per unit, in place; see ks_large.cu): used for state
 // dimensions the column-owner kernels cannot hold in shared memory, up to LARGE_NMAX, with

@@ -169,6 +169,11 @@ struct TcSmem {   // byte offsets inside the block's tensor-core region
 // Xb^T_hi V_lo] (64 columns), D2 (up to 128 columns).
 constexpr uint32_t TM_A1H = 0, TM_A1L = 128, TM_D1 = 256, TM_D2 = 384, TM_COLS = 512;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 20;   // polls; about a second at most
+// Test-only stall mode (KS_TEST_STALL_TC=1, level kernels): the first chunk of each block issues
+// no MMA and no commit, so its completion wait can only run out.  That exercises the timeout
+// path (ST_TIMEOUT, abort flag, TMEM still freed) with nothing in flight on the tensor cores;
+// the shorter limit keeps the test quick.
+constexpr uint32_t TC_STALL_TEST_LIMIT = 1u << 14;
 constexpr int TC_CW = 128;                 // columns per tensor-core chunk
 
 struct TcState {
@@ -176,15 +181,18 @@ struct TcState {
     uint32_t tmem;                         // first of TM_COLS allocated columns
     uint32_t phase;                        // parity of the next completion to wait for
     unsigned long long* bad;               // error words for ST_TIMEOUT
+    int stall;                             // test-only stall mode (see TC_STALL_TEST_LIMIT)
 };
 
 __host__ __device__ inline size_t tc_align(size_t b) { return (b + 127) & ~(size_t)127; }
 
 // Whole block: allocate TMEM (warp 0), initialise the completion barrier.
-__device__ void tc_setup(TcState& tc, unsigned char* region, unsigned long long* bad) {
+__device__ void tc_setup(TcState& tc, unsigned char* region, unsigned long long* bad,
+                         int stall = 0) {
     tc.smem = region;
     tc.phase = 0;
     tc.bad = bad;
+    tc.stall = stall;
     uint32_t* slot = reinterpret_cast<uint32_t*>(region + TcSmem::SLOT);
     if (threadIdx.x < 32) {
         tc::tmem_alloc(slot, TM_COLS);
@@ -213,7 +221,8 @@ __device__ void tc_wait(TcState& tc) {
     int* abort = reinterpret_cast<int*>(tc.smem + TcSmem::ABORT);
     bool ok = true;
     if (!*abort)
-        ok = tc::mbar_wait(reinterpret_cast<uint64_t*>(tc.smem + TcSmem::MBAR), tc.phase, TC_WAIT_LIMIT);
+        ok = tc::mbar_wait(reinterpret_cast<uint64_t*>(tc.smem + TcSmem::MBAR), tc.phase,
+                           tc.stall ? TC_STALL_TEST_LIMIT : TC_WAIT_LIMIT);
     tc.phase ^= 1u;
     if (__syncthreads_or(!ok) && threadIdx.x == 0) {
         if (!*abort && tc.bad != nullptr) flag_error(tc.bad, ST_TIMEOUT, 0);
@@ -351,8 +360,9 @@ __device__ void tc_apply_chunk(const TcChunk& ch, int kk0, int bw, int p, const 
     tc::fence_before();
     __syncthreads();
     // 2. D1 (M = 128 columns c, K = KP rows): one N = 64 product Xb^T_hi [V_hi | V_lo] and one
-    //    N = 32 product Xb^T_lo V_hi into its first 32 columns, per K = 8 step.
-    if (tid == 0 && !*abort) {
+    //    N = 32 product Xb^T_lo V_hi into its first 32 columns, per K = 8 step.  (In the
+    //    test-only stall mode nothing is issued, so the wait below runs out.)
+    if (tid == 0 && !*abort && !tc.stall) {
         tc::fence_after();
         const uint32_t id64 = tc::idesc_tf32(128, 2 * PB), id32 = tc::idesc_tf32(128, PB);
         const uint64_t b0 = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::B1), 2 * PB, 0);
@@ -1128,12 +1138,12 @@ __global__ void __launch_bounds__(NTH) whiten_k(WhitenArgs a, int tc_off) {
 template <typename T>
 __global__ void __launch_bounds__(NTH) level_k(int n, int64_t nc, int level, T* in, T* out, T* R,
                                                double* resid, const double* cn2, const double* cd2,
-                                               unsigned long long* bad, int tc_off) {
+                                               unsigned long long* bad, int tc_off, int stall) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TcState tcs;
     TcState* tc = nullptr;
     if (sizeof(T) == 4 && tc_off >= 0) {
-        tc_setup(tcs, smem_raw + tc_off, bad);
+        tc_setup(tcs, smem_raw + tc_off, bad, stall);
         tc = &tcs;
     }
     for (int64_t t = blockIdx.x; t < nc / 2; t += gridDim.x)
@@ -1205,6 +1215,11 @@ bool tc_enabled() {
     const char* v = getenv("KS_NO_TC");
     return !(v && *v && *v != '0');
 }
+// Test-only: KS_TEST_STALL_TC=1 makes the tensor-core level kernels take the stall mode.
+int tc_stall_test() {
+    const char* v = getenv("KS_TEST_STALL_TC");
+    return (v && *v && *v != '0') ? 1 : 0;
+}
 // Shared memory of an FP32 kernel whose own layout takes `base` bytes: the tensor-core region
 // follows at tc_align(base); *off receives that offset (-1 without tensor cores).
 size_t with_tc(size_t base, bool fp32, int* off) {
@@ -1256,10 +1271,11 @@ cudaError_t launch_level_large(int n, int64_t nc, int level, void* in, void* out
     const unsigned grid = grid_of(nc / 2, tc_off >= 0 ? 1 : 2);
     if (fp32) {
         set_smem(level_k<float>, smem);
-        level_k<float><<<grid, NTH, smem, st>>>(n, nc, level, (float*)in, (float*)out, (float*)R, resid, cn2, cd2, bad, tc_off);
+        const int stall = tc_off >= 0 ? tc_stall_test() : 0;
+        level_k<float><<<grid, NTH, smem, st>>>(n, nc, level, (float*)in, (float*)out, (float*)R, resid, cn2, cd2, bad, tc_off, stall);
     } else {
         set_smem(level_k<double>, smem);
-        level_k<double><<<grid, NTH, smem, st>>>(n, nc, level, (double*)in, (double*)out, (double*)R, resid, cn2, cd2, bad, -1);
+        level_k<double><<<grid, NTH, smem, st>>>(n, nc, level, (double*)in, (double*)out, (double*)R, resid, cn2, cd2, bad, -1, 0);
     }
     ++t_launches;
     return cudaGetLastError();

@@ -114,6 +114,8 @@ struct ks_server {
     std::deque<Tick> inflight;
     std::vector<cudaEvent_t> events;
     int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_ticks = 0, n_launches = 0;
+    int64_t n_shared_launches = 0;   // launches that carried work of two or more requests
+    int64_t max_per_launch = 0;      // most requests carried by one launch
     std::string err;
 };
 
@@ -364,6 +366,11 @@ void issue_tick(ks_server* S, const std::vector<Req*>& sched) {
     }
     S->n_launches += (int64_t)launches.size();
     S->n_ticks++;
+    for (const Launch& L : launches) {
+        const int64_t np = (int64_t)L.idx.size();
+        if (np >= 2) S->n_shared_launches++;
+        if (np > S->max_per_launch) S->max_per_launch = np;
+    }
     ks_server::Tick t;
     t.ev = take_event(S);
     t.buf = b;
@@ -401,11 +408,10 @@ void complete_oldest(ks_server* S) {
         }
         cudaStreamSynchronize(S->cst);
         std::lock_guard<std::mutex> lk(S->mu);
-        static const int order[] = {ST_NOT_SPD, ST_SINGULAR, ST_TIMEOUT, ST_ARG};
-        const auto now = Clock::now();
+            const auto now = Clock::now();
         for (size_t i = 0; i < t.finishing.size(); ++i) {
             Req* r = t.finishing[i];
-            for (int code : order)
+            for (int code : status_order)
                 if (words[i * ST_NCODES + code] != ~0ULL) {
                     r->status = code;
                     r->info = (int64_t)words[i * ST_NCODES + code];
@@ -765,6 +771,8 @@ ks_status ks_server_stats(ks_server* S, ks_server_counters* out) {
     out->queued = (int64_t)S->queue.size();
     out->ticks = S->n_ticks;
     out->launches = S->n_launches;
+    out->shared_launches = S->n_shared_launches;
+    out->max_requests_per_launch = S->max_per_launch;
     out->bytes_in_use = S->used;
     out->bytes_budget = S->opt.mem_budget;
     return KS_OK;

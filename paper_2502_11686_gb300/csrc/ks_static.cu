@@ -76,6 +76,14 @@ extern "C" ks_status ks_smooth_static(int device, void* stream, int64_t k, int n
     const size_t cs = nt + 2 * (size_t)n + 2 * (size_t)n * n;   // level record
     const size_t rs = nt + 2 * (size_t)n * n + n;               // R record
     const size_t ss = 2 * (size_t)n * n;                        // SelInv record
+    // Every state needs at least one level record and one R record, so a k above this bound
+    // cannot fit; rejecting it first also keeps the byte counts below from overflowing.
+    const int64_t k_fit = (int64_t)(KS_STATIC_SCRATCH_BYTES / (sizeof(double) * (cs + rs)));
+    if (k > k_fit)
+        return report(err, err_len, KS_ERR_ARG,
+                      "k = %lld, n = %d needs more work memory than the %zu bytes of the static "
+                      "scratch array (at most %lld states at this n); use ks_smooth for this size",
+                      (long long)k, n, (size_t)KS_STATIC_SCRATCH_BYTES, (long long)k_fit);
     size_t off = 0;
     const size_t o_bad = off; off += round256(sizeof(unsigned long long) * ST_NCODES);
     const size_t o_a = off;   off += round256((size_t)k * cs * sizeof(double));
@@ -128,6 +136,17 @@ extern "C" ks_status ks_smooth_static(int device, void* stream, int64_t k, int n
     }
     char* ws = static_cast<char*>(base);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // The call ends by waiting for its own work on `stream`; a wait inside a stream capture
+    // would invalidate the caller's capture, so a capturing stream is refused up front.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return report(err, err_len, KS_ERR_CUDA, "cudaStreamIsCapturing failed");
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return report(err, err_len, KS_ERR_ARG,
+                      "stream is capturing; ks_smooth_static synchronizes its stream and cannot "
+                      "run inside a capture");
     unsigned long long* bad = reinterpret_cast<unsigned long long*>(ws + o_bad);
     double* resid = reinterpret_cast<double*>(ws + o_res);
     const SmallOps* ops = small_ops(n);
@@ -177,14 +196,12 @@ extern "C" ks_status ks_smooth_static(int device, void* stream, int64_t k, int n
     KS_STATIC_CUDA(cudaMemcpyAsync(words, bad, sizeof(words), cudaMemcpyDeviceToHost, st));
     KS_STATIC_CUDA(cudaStreamSynchronize(st));
 #undef KS_STATIC_CUDA
-    static const int order[] = {ST_NOT_SPD, ST_SINGULAR, ST_TIMEOUT, ST_ARG};
-    for (int code : order)
+    for (int code : status_order) {
         if (words[code] != ~0ULL) {
             if (info) *info = (int64_t)words[code];
-            return report(err, err_len, (ks_status)code, "%s %lld",
-                          code == ST_NOT_SPD ? "a covariance matrix is not SPD at step"
-                                             : "singular diagonal block of R at state",
+            return report(err, err_len, (ks_status)code, "%s %lld", status_message(code),
                           (long long)words[code]);
         }
+    }
     return KS_OK;
 }

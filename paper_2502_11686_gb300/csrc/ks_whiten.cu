@@ -44,4 +44,49 @@ cudaError_t launch_whiten(const WhitenArgs& a, bool fp32, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Non-finite inputs.  NaN or Inf in F_i, H_{i-1} or G_i reaches the column norms cn2 / cd2 of
+// state i through the whitening (a non-finite K_i or C_i is already caught by its Cholesky
+// factorization); o_i and c_i enter only the right-hand side and are checked directly.
+__global__ void check_finite_kernel(WhitenArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = a.n;
+    const int64_t kn = a.k * n;
+    for (int64_t e = t0; e < kn; e += stride)
+        if (!isfinite(a.cn2[e]) || !isfinite(a.cd2[e])) flag_error(a.bad, ST_NONFINITE, e / n);
+    if (a.c != nullptr)
+        for (int64_t e = t0; e < (a.k - 1) * n; e += stride)
+            if (!isfinite(a.c[e])) flag_error(a.bad, ST_NONFINITE, e / n);
+    if (a.o != nullptr) {
+        const int64_t tot = a.m_uniform >= 0 ? a.k * a.m_uniform : a.goff[a.k];
+        for (int64_t e = t0; e < tot; e += stride) {
+            if (isfinite(a.o[e])) continue;
+            int64_t i;
+            if (a.m_uniform >= 0) {
+                i = e / a.m_uniform;
+            } else {   // the step whose rows hold entry e: goff[i] <= e < goff[i + 1]
+                int64_t lo = 0, hi = a.k;
+                while (hi - lo > 1) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (a.goff[mid] <= e) lo = mid; else hi = mid;
+                }
+                i = lo;
+            }
+            flag_error(a.bad, ST_NONFINITE, i);
+        }
+    }
+}
+
+cudaError_t launch_check_finite(const WhitenArgs& a, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (a.k * a.n + 255) / 256;
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+    const unsigned grid = (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+    check_finite_kernel<<<grid, 256, 0, st>>>(a);
+    ++t_launches;
+    return cudaGetLastError();
+}
+
 }  // namespace ks

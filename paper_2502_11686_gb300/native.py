@@ -14,9 +14,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libks.so")
 
 KS_OK, KS_ERR_ARG, KS_ERR_NOT_SPD, KS_ERR_SINGULAR, KS_ERR_OOM, KS_ERR_CUDA, KS_ERR_TIMEOUT, \
-    KS_ERR_NO_FACTOR = range(8)
+    KS_ERR_NO_FACTOR, KS_ERR_NONFINITE = range(9)
 STATUS_NAMES = {0: "KS_OK", 1: "KS_ERR_ARG", 2: "KS_ERR_NOT_SPD", 3: "KS_ERR_SINGULAR",
-                4: "KS_ERR_OOM", 5: "KS_ERR_CUDA", 6: "KS_ERR_TIMEOUT", 7: "KS_ERR_NO_FACTOR"}
+                4: "KS_ERR_OOM", 5: "KS_ERR_CUDA", 6: "KS_ERR_TIMEOUT", 7: "KS_ERR_NO_FACTOR",
+                8: "KS_ERR_NONFINITE"}
 KS_FP64, KS_FP32_REFINE = 0, 1
 KS_TI_F, KS_TI_H, KS_TI_K, KS_TI_G, KS_TI_C = 1, 2, 4, 8, 16
 
@@ -26,7 +27,7 @@ EXPORTS = ("ks_default_options", "ks_create", "ks_smooth", "ks_covariances", "ks
            "ks_profile_read", "ks_smooth_static", "ks_smooth_batch", "ks_generate",
            "ks_server_create", "ks_server_submit", "ks_server_submit_synthetic",
            "ks_server_covariances", "ks_server_wait", "ks_server_result", "ks_server_release",
-           "ks_server_stats", "ks_server_destroy")
+           "ks_server_stats", "ks_server_destroy", "ks_measure_fma_rate")
 PHASES = ("whiten", "level", "backsub", "refine", "selinv", "copy", "batch")
 
 
@@ -66,7 +67,8 @@ class ks_server_counters(ctypes.Structure):
                 ("completed", ctypes.c_int64), ("active", ctypes.c_int64),
                 ("queued", ctypes.c_int64), ("ticks", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
-                ("bytes_budget", ctypes.c_size_t)]
+                ("bytes_budget", ctypes.c_size_t), ("shared_launches", ctypes.c_int64),
+                ("max_requests_per_launch", ctypes.c_int64)]
 
 
 class KsError(RuntimeError):
@@ -143,6 +145,8 @@ def load():
         lib.ks_server_stats.restype = I
         lib.ks_server_destroy.argtypes = [P]
         lib.ks_server_destroy.restype = I
+        lib.ks_measure_fma_rate.argtypes = [I, I, ctypes.POINTER(ctypes.c_double)]
+        lib.ks_measure_fma_rate.restype = I
         _lib = lib
         return lib
 
@@ -347,3 +351,12 @@ def ks_smooth_batch(ctx, problems, check=True):
         raise KsError(st, ks_last_error(ctx) + f" (problems {bad[:8]})",
                       info_arr[bad[0]] if bad else -1)
     return st, list(st_arr), list(info_arr)
+
+
+def ks_measure_fma_rate(device, precision) -> float:
+    """Measured FMA rate of the device in TFLOP/s (FP64 for KS_FP64, FP32 otherwise)."""
+    v = ctypes.c_double(0.0)
+    st = load().ks_measure_fma_rate(int(device), int(precision), ctypes.byref(v))
+    if st != KS_OK:
+        raise KsError(st, "ks_measure_fma_rate failed")
+    return v.value

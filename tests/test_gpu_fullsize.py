@@ -1,0 +1,104 @@
+"""Parity with the oracle at sizes where the kernels take their full-size paths.
+
+At k = 700 the first level of an n = 128 problem has 350 tiles, so each of the 152 persistent
+blocks of the large-state level kernel (one block per SM while it holds the tensor memory)
+works through two or three tiles, and the in-place records no longer fit in L2 at once; the
+tensor-core chunk loop runs exactly as in the benchmarked workload.  The same inputs are
+smoothed in FP64, in FP32 + refinement with the tcgen05 trailing updates, and with the CUDA-core
+updates (KS_NO_TC=1), each against one oracle run: states (global and per state), every
+covariance block and every lag-one block.  Also: n = 96 with ragged observation counts
+(including steps without observations), FP64 n = 48 at k = 5000 (m = 48 and m = 24), and the
+lag-one blocks of the register-column path (n = 16).
+Bounds as in parity.py; the FP32 covariance bounds are per workload (COV32).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_11686_gb300 import Smoother, inputs, problem_arrays
+from parity import TOL32_STATES, TOL64, check_blocks, check_states
+
+pytestmark = pytest.mark.gpu
+
+COV32 = {"n128": 1e-3, "n96": 1e-3}
+
+
+def run(precision, p, monkeypatch=None, no_tc=False):
+    if monkeypatch is not None:
+        monkeypatch.setenv("KS_NO_TC", "1" if no_tc else "0")
+    with Smoother(device=0, precision=precision) as sm:
+        arr = problem_arrays(p, "cuda")
+        u, h = sm.smooth(p.k, p.n, arr, keep=True)
+        cov, cross = sm.covariances(h, p.k, p.n, arr["F"], cross=True)
+        r2 = sm.residual(h)
+        sm.release(h)
+    return u.cpu().numpy(), cov.cpu().numpy(), cross.cpu().numpy(), r2
+
+
+@pytest.fixture(scope="module")
+def n128():
+    p = inputs.random_problem(700, 128, 128, seed=700128, with_c=True, f_scale=0.995)
+    return p, oracle.smooth(p, cross=True)
+
+
+def test_n128_fp64_full_size(n128):
+    p, ref = n128
+    u, cov, cross, r2 = run("fp64", p)
+    check_states(u, ref["u"], TOL64)
+    check_blocks(cov, ref["cov"], TOL64)
+    check_blocks(cross, ref["cross"], TOL64, "cross")
+    assert abs(r2 - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"])
+
+
+@pytest.mark.parametrize("no_tc", [False, True], ids=["tcgen05", "cuda_cores"])
+def test_n128_fp32_refine_full_size(n128, no_tc, monkeypatch):
+    p, ref = n128
+    u, cov, cross, _ = run("fp32_refine", p, monkeypatch, no_tc)
+    check_states(u, ref["u"], TOL32_STATES)
+    check_blocks(cov, ref["cov"], COV32["n128"])
+    check_blocks(cross, ref["cross"], COV32["n128"], "cross")
+
+
+@pytest.fixture(scope="module")
+def n96_ragged():
+    rng = np.random.default_rng(96)
+    k, n = 700, 96
+    m = rng.integers(0, n + 1, size=k).astype(np.int32)
+    m[0] = n
+    m[rng.integers(1, k, size=20)] = 0
+    p = inputs.random_problem(k, n, m, seed=70096, with_c=True, f_scale=0.99)
+    return p, oracle.smooth(p, cross=True)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_n96_ragged_full_size(n96_ragged, precision):
+    p, ref = n96_ragged
+    u, cov, cross, _ = run(precision, p)
+    if precision == "fp64":
+        check_states(u, ref["u"], TOL64)
+        check_blocks(cov, ref["cov"], TOL64)
+        check_blocks(cross, ref["cross"], TOL64, "cross")
+    else:
+        check_states(u, ref["u"], TOL32_STATES)
+        check_blocks(cov, ref["cov"], COV32["n96"])
+
+
+@pytest.mark.parametrize("m", [48, 24])
+def test_n48_fp64_k5000(m):
+    p = inputs.random_problem(5000, 48, m, seed=5000 + m, with_c=True, f_scale=0.995)
+    ref = oracle.smooth(p, cross=True)
+    u, cov, cross, r2 = run("fp64", p)
+    check_states(u, ref["u"], TOL64)
+    check_blocks(cov, ref["cov"], TOL64)
+    check_blocks(cross, ref["cross"], TOL64, "cross")
+    assert abs(r2 - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"])
+
+
+@pytest.mark.parametrize("n", [16, 48])
+def test_lag_one_blocks_register_column_path(n):
+    p = inputs.random_problem(1500, n, n, seed=1500 + n, with_c=True, f_scale=0.99)
+    ref = oracle.smooth(p, cross=True)
+    u, cov, cross, _ = run("fp64", p)
+    check_states(u, ref["u"], TOL64)
+    check_blocks(cov, ref["cov"], TOL64)
+    check_blocks(cross, ref["cross"], TOL64, "cross")

@@ -1,29 +1,21 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle, element by element.
 
-Tolerances (FP64 mode): relative error <= 1e-10 for the states (2-norm over the concatenated
-vector) and for every covariance block (Frobenius norm per block, worst block).  FP32 +
-refinement mode: states <= 1e-6; the FP32 covariances carry ~cond * 6e-8 and are bounded
-loosely (the paper fixes no FP32 target).
+Error measures and bounds are those of ``parity.py``: FP64 states (global and per state) and
+every covariance block <= 1e-10 relative; FP32 + refinement states <= 1e-6 (global and per
+state); FP32 covariances bounded per workload (COV32 below) at about ten times the error
+measured on GB300 (the paper fixes no FP32 target).
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2502_11686_gb300 import Smoother, inputs, native, problem_arrays
+from parity import TOL32_STATES, TOL64, check_blocks, check_states
 
 pytestmark = pytest.mark.gpu
 
-TOL64 = 1e-10
-
-
-def rel_states(u, ref):
-    return float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
-
-
-def rel_cov(c, ref):
-    num = np.linalg.norm((c - ref).reshape(len(ref), -1), axis=1)
-    den = np.linalg.norm(ref.reshape(len(ref), -1), axis=1)
-    return float(np.max(num / den))
+# FP32 covariance bounds per workload (worst covariance block, relative Frobenius error).
+COV32 = {"grid": 1e-5, "long_n6": 1e-5, "n48": 1e-4, "n16_m8": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -75,10 +67,10 @@ def test_fp64_grid(sm64, n, tail_mode):
         p = inputs.random_problem(k, n, n, seed=1000 * n + k, with_c=True)
         ref = oracle.smooth(p, cross=True)
         got = run(sm64, p, cross=True)
-        assert rel_states(got["u"], ref["u"]) < TOL64, (k, n)
-        assert rel_cov(got["cov"], ref["cov"]) < TOL64, (k, n)
+        check_states(got["u"], ref["u"], TOL64, f" k={k} n={n}")
+        check_blocks(got["cov"], ref["cov"], TOL64)
         if k > 1:
-            assert rel_cov(got["cross"], ref["cross"]) < TOL64, (k, n)
+            check_blocks(got["cross"], ref["cross"], TOL64, "cross")
         assert abs(got["resid2"] - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"]), (k, n)
 
 
@@ -101,8 +93,8 @@ def test_fp64_ragged_observations(sm64, pattern, k, tail_mode):
     p = inputs.random_problem(k, n, m, seed=k + 3, with_c=True)
     ref = oracle.smooth(p)
     got = run(sm64, p)
-    assert rel_states(got["u"], ref["u"]) < TOL64
-    assert rel_cov(got["cov"], ref["cov"]) < TOL64
+    check_states(got["u"], ref["u"], TOL64)
+    check_blocks(got["cov"], ref["cov"], TOL64)
 
 
 def test_fp64_constant_velocity_workload(sm64, tail_mode):
@@ -110,9 +102,9 @@ def test_fp64_constant_velocity_workload(sm64, tail_mode):
     p = inputs.cv_problem(k=1000, seed=0)
     ref = oracle.smooth(p, cross=True)
     got = run(sm64, p, cross=True)
-    assert rel_states(got["u"], ref["u"]) < TOL64
-    assert rel_cov(got["cov"], ref["cov"]) < TOL64
-    assert rel_cov(got["cross"], ref["cross"]) < TOL64
+    check_states(got["u"], ref["u"], TOL64)
+    check_blocks(got["cov"], ref["cov"], TOL64)
+    check_blocks(got["cross"], ref["cross"], TOL64, "cross")
 
 
 @pytest.mark.parametrize("m", [48, 24])
@@ -120,8 +112,8 @@ def test_fp64_dense_blocks_n48(sm64, m):
     p = inputs.random_problem(129, 48, m, seed=m, f_scale=0.995)
     ref = oracle.smooth(p)
     got = run(sm64, p)
-    assert rel_states(got["u"], ref["u"]) < TOL64
-    assert rel_cov(got["cov"], ref["cov"]) < TOL64
+    check_states(got["u"], ref["u"], TOL64)
+    check_blocks(got["cov"], ref["cov"], TOL64)
 
 
 def test_fp64_max_n(sm64):
@@ -129,17 +121,18 @@ def test_fp64_max_n(sm64):
     p = inputs.random_problem(11, n, n, seed=5)
     ref = oracle.smooth(p)
     got = run(sm64, p)
-    assert rel_states(got["u"], ref["u"]) < TOL64
-    assert rel_cov(got["cov"], ref["cov"]) < TOL64
+    check_states(got["u"], ref["u"], TOL64)
+    check_blocks(got["cov"], ref["cov"], TOL64)
 
 
 def test_fp64_full_size_long_problem(sm64):
     """k = 1,000,000, n = m = 6: every state and every covariance block against the oracle."""
     p = inputs.random_problem(1_000_000, 6, 6, seed=0, f_scale=0.99)
-    ref = oracle.smooth(p)
-    got = run(sm64, p)
-    assert rel_states(got["u"], ref["u"]) < TOL64
-    assert rel_cov(got["cov"], ref["cov"]) < TOL64
+    ref = oracle.smooth(p, cross=True)
+    got = run(sm64, p, cross=True)
+    check_states(got["u"], ref["u"], TOL64)
+    check_blocks(got["cov"], ref["cov"], TOL64)
+    check_blocks(got["cross"], ref["cross"], TOL64, "cross")
 
 
 def test_host_and_device_pointers_agree_bitwise(sm64):
@@ -161,7 +154,7 @@ def test_deterministic(sm64):
 def test_exact_recovery(sm64):
     p = inputs.consistent_problem(3001, 4, 4, seed=2)
     got = run(sm64, p, cov=False)
-    assert rel_states(got["u"], p.truth) < TOL64
+    check_states(got["u"], p.truth, TOL64)
     assert got["resid2"] < 1e-18 * float(np.sum(p.o ** 2))
 
 
@@ -204,14 +197,15 @@ def test_refine_grid(sm32, n, tail_mode):
         p = inputs.random_problem(k, n, n, seed=77 * n + k, with_c=True)
         ref = oracle.smooth(p)
         got = run(sm32, p)
-        assert rel_states(got["u"], ref["u"]) < 1e-6, (k, n)
-        assert rel_cov(got["cov"], ref["cov"]) < 1e-3, (k, n)
+        check_states(got["u"], ref["u"], TOL32_STATES, f" k={k} n={n}")
+        check_blocks(got["cov"], ref["cov"], COV32["grid"])
 
 
-@pytest.mark.parametrize("n,m,k", [(6, 6, 100_000), (48, 48, 600), (48, 24, 600), (16, 8, 3000)])
-def test_refine_workloads(sm32, n, m, k):
+@pytest.mark.parametrize("n,m,k,cls", [(6, 6, 100_000, "long_n6"), (48, 48, 600, "n48"),
+                                       (48, 24, 600, "n48"), (16, 8, 3000, "n16_m8")])
+def test_refine_workloads(sm32, n, m, k, cls):
     p = inputs.random_problem(k, n, m, seed=n + m, f_scale=0.995 if n == 48 else 0.99)
     ref = oracle.smooth(p)
     got = run(sm32, p)
-    assert rel_states(got["u"], ref["u"]) < 1e-6
-    assert rel_cov(got["cov"], ref["cov"]) < 1e-3
+    check_states(got["u"], ref["u"], TOL32_STATES)
+    check_blocks(got["cov"], ref["cov"], COV32[cls])

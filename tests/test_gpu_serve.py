@@ -63,9 +63,13 @@ def problems():
     return out
 
 
-def test_each_result_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+def test_each_result_same_alone_and_in_the_mix(precision):
+    """Each request's result equals the same problem smoothed alone (and the oracle's), and the
+    requests really ran together: some launches carried the work of several requests."""
     probs = problems()
-    with Smoother(device=0, precision="fp64") as sm:
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    with Smoother(device=0, precision=precision) as sm:
         refs = [alone(sm, p, c) for p, c in probs]
         srv = native.ks_server_create(sm.ctx)
         reqs = [request(p, c) for p, c in probs]
@@ -85,12 +89,13 @@ def test_each_result_same_alone_and_in_the_mix():
         native.ks_server_destroy(srv)
     assert all(i["status"] == native.KS_OK and i["done"] for i in infos)
     assert stats["completed"] == len(probs) and stats["ticks"] > 0
+    assert stats["max_requests_per_launch"] >= 2 and stats["shared_launches"] > 0, stats
     for (p, want_cov), r, (u_ref, cov_ref) in zip(probs, reqs, refs):
         u = r["u_out"].cpu().numpy()
-        assert rel(u, u_ref) < 1e-10, (p.k, p.n)
-        assert rel(u, oracle.smooth(p, covariances=False)["u"]) < 1e-10
+        assert rel(u, u_ref) < tol, (p.k, p.n)
+        assert rel(u, oracle.smooth(p, covariances=False)["u"]) < tol
         if want_cov:
-            assert rel_blocks(r["cov_out"].cpu().numpy(), cov_ref) < 1e-10
+            assert rel_blocks(r["cov_out"].cpu().numpy(), cov_ref) < (1e-10 if precision == "fp64" else 1e-4)
 
 
 def test_covariance_follow_up_on_kept_factor():

@@ -55,6 +55,33 @@ def test_two_calls_in_a_row_match_ks_smooth():
         assert blk.max() < TOL
 
 
+def test_large_call_then_smaller_different_shape():
+    """A large call fills most of the shared array; the smaller call that follows has another n
+    and m, so it would read stale records of the first if any slot were not rewritten."""
+    first = inputs.random_problem(3000, 6, 6, seed=11, with_c=True)
+    second = inputs.random_problem(501, 3, 1, seed=12, with_c=True)
+    _static(first)
+    u_ref, cov_ref = _reference(second)
+    u, cov = _static(second)
+    assert _rel(u, u_ref) < TOL
+    blk = np.linalg.norm((cov - cov_ref).reshape(second.k, -1), axis=1) / \
+        np.linalg.norm(cov_ref.reshape(second.k, -1), axis=1)
+    assert blk.max() < TOL
+    # no observations at all: the states are not determined, and both entry points say so
+    none = inputs.random_problem(64, 2, 0, seed=13)
+    import torch
+    arr = problem_arrays(none, "cuda")
+    u0 = torch.empty((none.k, none.n), dtype=torch.float64, device="cuda")
+    st, _, msg = native.ks_smooth_static(0, None, none.k, none.n, 0, arr["F"], arr["H"], None,
+                                         arr["K"], None, None, None, u0, None)
+    assert st == native.KS_ERR_SINGULAR, (st, msg)
+    assert "singular" in msg
+    with Smoother(device=0, precision="fp64") as sm:
+        st2, _, _ = native.ks_smooth(sm.ctx, none.k, none.n, np.zeros(none.k, np.int32), arr["F"],
+                                     arr["H"], None, arr["K"], None, None, None, u0, check=False)
+    assert st2 == native.KS_ERR_SINGULAR
+
+
 def test_states_only_and_size_limit():
     p = inputs.random_problem(2049, 3, 2, seed=5)
     u_ref, _ = _reference(p)
@@ -64,4 +91,7 @@ def test_states_only_and_size_limit():
     big = 10_000_000
     u = torch.empty((1, 6), dtype=torch.float64, device="cuda")
     st, _, msg = native.ks_smooth_static(0, None, big, 6, 6, u, u, None, u, u, u, u, u, None)
+    assert st == native.KS_ERR_ARG and "static scratch" in msg
+    # a k whose byte count would overflow 64 bits is refused before any size arithmetic
+    st, _, msg = native.ks_smooth_static(0, None, 1 << 61, 1, 1, u, u, None, u, u, u, u, u, None)
     assert st == native.KS_ERR_ARG and "static scratch" in msg
