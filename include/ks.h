@@ -132,6 +132,30 @@ ks_status ks_smooth(ks_ctx *ctx, int64_t k, int n, const int32_t *m,
                     const double *G, const double *o, const double *C,
                     double *u_out, ks_handle *keep, int64_t *info);
 
+/*
+ * Smoothed states of a problem whose state dimension varies from step to step (Section 2: u_i
+ * has n_i entries; evolution equation i has l_i rows, H_i u_{i+1} = F_i u_i + c_i + eps_i with
+ * H_i of size l_i x n_{i+1} -- rectangular when the dimension changes -- and F_i of size
+ * l_i x n_i; Section 3 allows blocks of any size).
+ *   nd [k], l [k-1], m [k]: host int32 arrays of n_i (>= 1), l_i (>= 0), m_i (>= 0).
+ *   Packed FP64 row-major arrays in step order: F (l_i*n_i values per equation), H (l_i*n_{i+1}),
+ *   c (l_i, or NULL = 0), K (l_i*l_i, SPD), G (m_i*n_i per observation), o (m_i), C (m_i*m_i).
+ *   u_out: packed [sum n_i].  keep / info as in ks_smooth (info indexes steps and states).
+ * Host or device pointers, as everywhere.  The problem is embedded on the device into a uniform
+ * one of dimension N = max(n_i, l_i) (every padding component pinned by a unit observation, so
+ * the results are exactly the original problem's) and smoothed by the same kernels; requires
+ * N <= ks_max_n(ctx) and m_i + N - n_i <= ks_max_m(ctx, N).  Work grows like N^3 per step.
+ */
+ks_status ks_smooth_var(ks_ctx *ctx, int64_t k, const int32_t *nd, const int32_t *l,
+                        const int32_t *m, const double *F, const double *H, const double *c,
+                        const double *K, const double *G, const double *o, const double *C,
+                        double *u_out, ks_handle *keep, int64_t *info);
+
+/* Covariances cov(u_hat_i) (n_i x n_i each, packed [sum n_i^2]) of a factorization kept by
+ * ks_smooth_var (Section 4, Algorithm 2 on the padded factor; the padding components are
+ * uncorrelated with the real ones and are dropped).  KS_ERR_ARG for a handle of ks_smooth. */
+ks_status ks_covariances_var(ks_ctx *ctx, ks_handle h, double *cov_out);
+
 /* Bits of ks_problem.time_invariant: the array holds ONE matrix used at every step (a
  * time-invariant model) instead of one per step.  G and C may be time invariant only if every
  * m_i is the same. */
@@ -175,6 +199,16 @@ ks_status ks_smooth_batch(ks_ctx *ctx, int nprob, const ks_problem *probs, int *
  */
 ks_status ks_generate(ks_ctx *ctx, int64_t k, int n, int m, uint64_t seed, double f_scale,
                       double *F, double *H, double *K, double *G, double *C, double *o);
+
+/*
+ * The same recipe with independent draws for every step (input generation for benchmarks; none of
+ * the smoother's arithmetic): F [k-1][n][n] = f_scale * Q (Q as in ks_generate, one draw per
+ * problem stored for every step), H [k-1][n][n] = I, and for every step K_i ([k-1][n][n]),
+ * C_i ([k][m][m]) = L L^T with their own L, G_i ([k][m][n]) ~ N(0, 1/n), o ([k][m]) ~ N(0, 1).
+ * Device pointers; the arrays are per step (time_invariant = 0).
+ */
+ks_status ks_generate_steps(ks_ctx *ctx, int64_t k, int n, int m, uint64_t seed, double f_scale,
+                            double *F, double *H, double *K, double *G, double *C, double *o);
 
 /*
  * Serving loop (continuous batching; the paper has no counterpart).  A server owns a scheduler

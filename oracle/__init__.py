@@ -54,6 +54,8 @@ def load_library(path: str):
     lib.oracle_smooth.restype = ctypes.c_int
     lib.oracle_smooth.argtypes = [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P, P,
                                   P, P, P, P, P]
+    lib.oracle_smooth_var.restype = ctypes.c_int
+    lib.oracle_smooth_var.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
     return lib
 
 
@@ -99,3 +101,30 @@ def smooth(prob, covariances: bool = True, cross: bool = False, lib=None):
         raise OracleError(st, info.value)
     return {"u": u, "cov": cov, "cross": (crs[: k - 1] if cross else None),
             "resid2": resid.value}
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def smooth_var(prob, covariances: bool = True, lib=None):
+    """Smoothed states (and covariances) of a problem whose state dimension varies per step
+    (``paper_2502_11686_gb300.inputs.VarProblem``: per-step n_i, evolution rows l_i, packed
+    arrays).  Returns ``u`` packed [sum n_i], ``cov`` packed [sum n_i^2] (or None) and
+    ``resid2``."""
+    lib = lib or _load()
+    k = int(prob.k)
+    nd, m = _i32(prob.nd), _i32(prob.m)
+    lv = _i32(prob.l) if k > 1 else _i32(np.zeros(1))
+    F, H, c, K = _f64(prob.F), _f64(prob.H), _f64(prob.c), _f64(prob.K)
+    G, o, C = _f64(prob.G), _f64(prob.o), _f64(prob.C)
+    u = np.zeros(int(nd.astype(np.int64).sum()))
+    cov = np.zeros(int((nd.astype(np.int64) ** 2).sum())) if covariances else None
+    resid = ctypes.c_double(0.0)
+    info = ctypes.c_int64(-1)
+    st = lib.oracle_smooth_var(k, _ptr(nd), _ptr(lv), _ptr(m), _ptr(F), _ptr(H), _ptr(c), _ptr(K),
+                               _ptr(G), _ptr(o), _ptr(C), _ptr(u), _ptr(cov), ctypes.byref(resid),
+                               ctypes.byref(info))
+    if st != 0:
+        raise OracleError(st, info.value)
+    return {"u": u, "cov": cov, "resid2": resid.value}

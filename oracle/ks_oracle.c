@@ -352,3 +352,177 @@ done:
     free(Snext); free(Scur); free(T); free(Sx);
     return status;
 }
+
+/*
+ * oracle_smooth_var: the same smoother when the state dimension varies from step to step and
+ * H_i is rectangular (Section 2: u_i has n_i entries; evolution equation i has l_i rows, with
+ * H_i of size l_i x n_{i+1} and F_i of size l_i x n_i; "the dimensions of block rows and block
+ * columns can vary", Section 3).  Written directly for ragged blocks -- no padding -- as the
+ * same left-to-right Paige-Saunders elimination, back substitution and Algorithm 1 (I = {j+1})
+ * as oracle_smooth.
+ *
+ * Packed row-major FP64 inputs, in step order:
+ *   nd [k] state dimensions; l [k-1] evolution rows; m [k] observation rows (host int32);
+ *   F : evolution i occupies l_i*n_i values;  H : l_i*n_{i+1};  c : l_i (or NULL = 0);
+ *   K : l_i*l_i;  G : m_i*n_i;  o : m_i;  C : m_i*m_i.
+ * Outputs: u packed sum n_i; cov packed sum n_i^2 (or NULL); resid2; info.
+ */
+int oracle_smooth_var(int64_t k, const int32_t *nd, const int32_t *l, const int32_t *m,
+                      const double *F, const double *H, const double *c, const double *K,
+                      const double *G, const double *o, const double *C, double *u, double *cov,
+                      double *resid2, int64_t *info) {
+    if (k < 1 || !nd || !m || !u || (k > 1 && (!l || !F || !H || !K))) return ORC_ARG;
+    int nmax = 0, lmax = 0, mmax = 0;
+    for (int64_t i = 0; i < k; i++) {
+        if (nd[i] < 1 || m[i] < 0) return ORC_ARG;
+        if (nd[i] > nmax) nmax = nd[i];
+        if (m[i] > mmax) mmax = m[i];
+        if (i + 1 < k) {
+            if (l[i] < 0) return ORC_ARG;
+            if (l[i] > lmax) lmax = l[i];
+        }
+    }
+    if (mmax > 0 && (!G || !o || !C)) return ORC_ARG;
+    /* Offsets of every block in the packed arrays and in the outputs. */
+    int64_t *uo = malloc(sizeof(int64_t) * (size_t)(k + 1));   /* u, and R rows */
+    int64_t *so = malloc(sizeof(int64_t) * (size_t)(k + 1));   /* n_i^2 blocks */
+    int64_t *ro = malloc(sizeof(int64_t) * (size_t)(k + 1));   /* R_{i,i+1}: n_i x n_{i+1} */
+    int d = nmax > lmax ? nmax : lmax;
+    if (mmax > d) d = mmax;
+    int cw = 2 * nmax + 1;                         /* widest [col i | col i+1 | rhs] */
+    int maxrows = nmax + mmax + lmax + 1;
+    double *Rdiag = NULL, *Roff = NULL, *y = NULL;
+    double *V = malloc(sizeof(double) * d * d);
+    double *work = malloc(sizeof(double) * 4 * d * d);
+    double *S = malloc(sizeof(double) * (size_t)maxrows * cw);
+    double *carry = malloc(sizeof(double) * (size_t)maxrows * (nmax + 1));
+    double *tmp = malloc(sizeof(double) * (size_t)(d + 1) * cw);
+    double *Snext = malloc(sizeof(double) * nmax * nmax), *Scur = malloc(sizeof(double) * nmax * nmax);
+    double *T = malloc(sizeof(double) * nmax * nmax), *Sx = malloc(sizeof(double) * nmax * nmax);
+    int status = ORC_OK;
+    int64_t where = -1;
+    double res = 0.0;
+    if (!uo || !so || !ro || !V || !work || !S || !carry || !tmp || !Snext || !Scur || !T || !Sx) {
+        status = ORC_OOM;
+        goto done;
+    }
+    uo[0] = so[0] = ro[0] = 0;
+    for (int64_t i = 0; i < k; i++) {
+        uo[i + 1] = uo[i] + nd[i];
+        so[i + 1] = so[i] + (int64_t)nd[i] * nd[i];
+        ro[i + 1] = ro[i] + (i + 1 < k ? (int64_t)nd[i] * nd[i + 1] : 0);
+    }
+    Rdiag = malloc(sizeof(double) * (size_t)so[k]);
+    Roff = malloc(sizeof(double) * (size_t)(ro[k] > 0 ? ro[k] : 1));
+    y = malloc(sizeof(double) * (size_t)uo[k]);
+    if (!Rdiag || !Roff || !y) { status = ORC_OOM; goto done; }
+
+    int64_t go = 0, gv = 0, co = 0;   /* offsets of observation i: rows (o), values (G), C */
+    int64_t fo = 0, ho = 0, eo = 0, ko = 0;   /* offsets of evolution i in F, H, c, K */
+    /* Column 0 starts with the whitened observation of u_0 (n_0 + 1 wide: block | rhs). */
+    int n0 = nd[0], cr = 0;
+    if (append_observation(n0, m[0], G + gv, o + go, C + co, carry, &cr, V, work, tmp)) {
+        status = ORC_NOT_SPD; where = 0; goto done;
+    }
+    go += m[0]; gv += (int64_t)m[0] * n0; co += (int64_t)m[0] * m[0];
+    compress_carry(n0, carry, &cr, &res);
+
+    for (int64_t i = 0; i + 1 < k; i++) {
+        const int ni = nd[i], nj = nd[i + 1], li = l[i];
+        const int w = ni + nj + 1;   /* [col i | col i+1 | rhs] */
+        const int rows = cr + li;
+        for (int r = 0; r < cr; r++) {
+            for (int q = 0; q < ni; q++) S[r * w + q] = carry[r * (ni + 1) + q];
+            for (int q = 0; q < nj; q++) S[r * w + ni + q] = 0.0;
+            S[r * w + ni + nj] = carry[r * (ni + 1) + ni];
+        }
+        if (li > 0) {
+            if (whitening_factor(li, K + ko, V, work)) { status = ORC_NOT_SPD; where = i; goto done; }
+            /* Whitened evolution equation i: V (H_i u_{i+1} - F_i u_i) = V c_i. */
+            for (int r = 0; r < li; r++) {
+                for (int q = 0; q < ni; q++) tmp[r * w + q] = -F[fo + (int64_t)r * ni + q];
+                for (int q = 0; q < nj; q++) tmp[r * w + ni + q] = H[ho + (int64_t)r * nj + q];
+                tmp[r * w + ni + nj] = c ? c[eo + r] : 0.0;
+            }
+            matmul_sq(li, w, V, tmp, S + (size_t)cr * w);
+        }
+        fo += (int64_t)li * ni; ho += (int64_t)li * nj; eo += li; ko += (int64_t)li * li;
+        if (rows < ni) { status = ORC_SINGULAR; where = i; goto done; }
+        householder(rows, w, ni, S);
+        for (int r = 0; r < ni; r++) {
+            for (int q = 0; q < ni; q++) Rdiag[so[i] + (int64_t)r * ni + q] = S[r * w + q];
+            for (int q = 0; q < nj; q++) Roff[ro[i] + (int64_t)r * nj + q] = S[r * w + ni + q];
+            y[uo[i] + r] = S[r * w + ni + nj];
+        }
+        /* Rows below the first n_i live in column i+1 only: they start its carry. */
+        int nc = 0;
+        for (int r = ni; r < rows; r++, nc++) {
+            for (int q = 0; q < nj; q++) carry[nc * (nj + 1) + q] = S[r * w + ni + q];
+            carry[nc * (nj + 1) + nj] = S[r * w + ni + nj];
+        }
+        const int mi = m[i + 1];
+        if (append_observation(nj, mi, G + gv, o + go, C + co, carry, &nc, V, work, tmp)) {
+            status = ORC_NOT_SPD; where = i + 1; goto done;
+        }
+        go += mi; gv += (int64_t)mi * nj; co += (int64_t)mi * mi;
+        compress_carry(nj, carry, &nc, &res);
+        cr = nc;
+    }
+    {
+        const int64_t i = k - 1;
+        const int ni = nd[i];
+        if (cr < ni) { status = ORC_SINGULAR; where = i; goto done; }
+        householder(cr, ni + 1, ni, carry);
+        for (int r = 0; r < ni; r++) {
+            for (int q = 0; q < ni; q++) Rdiag[so[i] + (int64_t)r * ni + q] = carry[r * (ni + 1) + q];
+            y[uo[i] + r] = carry[r * (ni + 1) + ni];
+        }
+    }
+    /* Back substitution: R_ii u_i = y_i - R_{i,i+1} u_{i+1}. */
+    for (int64_t i = k - 1; i >= 0; i--) {
+        const int ni = nd[i];
+        for (int r = 0; r < ni; r++) {
+            double s = y[uo[i] + r];
+            if (i + 1 < k)
+                for (int q = 0; q < nd[i + 1]; q++)
+                    s -= Roff[ro[i] + (int64_t)r * nd[i + 1] + q] * u[uo[i + 1] + q];
+            u[uo[i] + r] = s;
+        }
+        if (upper_solve_vec(ni, Rdiag + so[i], u + uo[i])) { status = ORC_SINGULAR; where = i; goto done; }
+    }
+    /* Algorithm 1 with I = {j+1} on ragged blocks: T = R_jj^{-1} R_{j,j+1} (n_j x n_{j+1}),
+     * S_{j,j+1} = -T S_{j+1,j+1}, S_jj = R_jj^{-1} R_jj^{-T} - S_{j,j+1} T^T. */
+    if (cov) {
+        int64_t j = k - 1;
+        int nb = nd[j];
+        if (rinv_rinvt(nb, Rdiag + so[j], Snext, work)) { status = ORC_SINGULAR; where = j; goto done; }
+        memcpy(cov + so[j], Snext, sizeof(double) * nb * nb);
+        for (j = k - 2; j >= 0; j--) {
+            const int na = nd[j];
+            memcpy(T, Roff + ro[j], sizeof(double) * na * nb);
+            if (upper_solve_mat(na, nb, Rdiag + so[j], T)) { status = ORC_SINGULAR; where = j; goto done; }
+            for (int r = 0; r < na; r++)
+                for (int q = 0; q < nb; q++) {
+                    double s = 0.0;
+                    for (int p = 0; p < nb; p++) s += T[r * nb + p] * Snext[p * nb + q];
+                    Sx[r * nb + q] = -s;
+                }
+            rinv_rinvt(na, Rdiag + so[j], Scur, work);
+            for (int r = 0; r < na; r++)
+                for (int q = 0; q < na; q++) {
+                    double s = 0.0;
+                    for (int p = 0; p < nb; p++) s += Sx[r * nb + p] * T[q * nb + p];
+                    Scur[r * na + q] -= s;
+                }
+            memcpy(cov + so[j], Scur, sizeof(double) * na * na);
+            memcpy(Snext, Scur, sizeof(double) * na * na);
+            nb = na;
+        }
+    }
+done:
+    if (resid2) *resid2 = res;
+    if (info) *info = where;
+    free(uo); free(so); free(ro); free(Rdiag); free(Roff); free(y); free(V); free(work); free(S);
+    free(carry); free(tmp); free(Snext); free(Scur); free(T); free(Sx);
+    return status;
+}

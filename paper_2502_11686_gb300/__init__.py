@@ -93,6 +93,33 @@ class Smoother:
         ks_covariances(self.ctx, h, cov, crs)
         return (cov, crs[: k - 1]) if cross else cov
 
+    def smooth_var(self, prob, device="cuda", covariances: bool = False):
+        """A variable-dimension problem (``inputs.VarProblem``): packed states (and packed
+        covariance blocks), as device tensors (device given) or numpy arrays (device None)."""
+        import numpy as np
+        arr = {nm: getattr(prob, nm) for nm in ("F", "H", "c", "K", "G", "o", "C")}
+        tot_u = int(np.asarray(prob.nd, dtype=np.int64).sum())
+        tot_s = int((np.asarray(prob.nd, dtype=np.int64) ** 2).sum())
+        if device is not None:
+            import torch
+            arr = {nm: (torch.from_numpy(np.ascontiguousarray(a)).to(device) if a is not None
+                        and a.size else None) for nm, a in arr.items()}
+            u = torch.empty(tot_u, dtype=torch.float64, device=device)
+            cov = torch.empty(max(tot_s, 1), dtype=torch.float64, device=device)
+        else:
+            arr = {nm: (np.ascontiguousarray(a) if a is not None and a.size else None)
+                   for nm, a in arr.items()}
+            u = np.empty(tot_u)
+            cov = np.empty(max(tot_s, 1))
+        _, h, _ = native.ks_smooth_var(self.ctx, prob.k, prob.nd, prob.l, prob.m, arr["F"],
+                                       arr["H"], arr["c"], arr["K"], arr["G"], arr["o"],
+                                       arr["C"], u, keep=covariances)
+        if not covariances:
+            return u
+        native.ks_covariances_var(self.ctx, h, cov)
+        ks_release(self.ctx, h)
+        return u, cov
+
     def residual(self, h) -> float:
         return ks_residual(self.ctx, h)
 

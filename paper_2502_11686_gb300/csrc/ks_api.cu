@@ -446,6 +446,7 @@ ks_status ks_destroy(ks_ctx* ctx) {
     for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
     ctx->graphs.clear();
     if (ctx->bmeta) cudaFree(ctx->bmeta);
+    if (ctx->vbuf) cudaFree(ctx->vbuf);
     for (ks_fac* f : ctx->facs) {
         cudaFree(f->R);
         cudaFree(f->resid);

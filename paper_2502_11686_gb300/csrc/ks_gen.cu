@@ -59,7 +59,8 @@ __device__ double uniform(uint64_t seed, uint32_t tag, uint64_t idx) {
     return u01(w[0], w[1]);
 }
 
-enum { TAG_V = 1, TAG_LK = 2, TAG_DK = 3, TAG_LC = 4, TAG_DC = 5, TAG_G = 6, TAG_O = 7 };
+enum { TAG_V = 1, TAG_LK = 2, TAG_DK = 3, TAG_LC = 4, TAG_DC = 5, TAG_G = 6, TAG_O = 7,
+       TAG_LKS = 8, TAG_DKS = 9, TAG_LCS = 10, TAG_DCS = 11, TAG_GS = 12 };
 
 // One block builds the time-invariant matrices.  Shared memory: the three reflection vectors
 // and the packed lower factor L of K or C (max(n, m)^2 / 2 doubles); F is formed in place in
@@ -140,6 +141,97 @@ cudaError_t launch_generate(int64_t k, int n, int m, uint64_t seed, double f_sca
         gen_obs_kernel<<<(unsigned)(b > 8192 ? 8192 : b), 256, 0, st>>>(count, seed, o);
         ++t_launches;
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Per-step draws (the batched-benchmark recipe): F_i = f Q for every step (Q as above, one draw
+// per problem, stored for every step so that its traffic is real), H_i = I, and K_i, C_i = L L^T
+// and G_i ~ N(0, 1/n) drawn independently for every step; o_i ~ N(0, 1).  Counters: array tag,
+// element index step * (matrix size) + entry.  Persistent blocks; each forms Q once in shared
+// memory and then writes the steps it owns.
+__device__ void gen_spd_into(double* out, double* Lp, int d, uint64_t seed, uint32_t tl,
+                             uint32_t td, uint64_t base) {
+    const int tid = threadIdx.x, nth = blockDim.x;
+    __syncthreads();
+    for (int e = tid; e < d * d; e += nth) {
+        const int r = e / d, c = e % d;
+        if (c <= r)
+            Lp[r * (r + 1) / 2 + c] = c < r ? 0.1 * gauss(seed, tl, base * d + e)
+                                            : 0.5 + uniform(seed, td, base + r);
+    }
+    __syncthreads();
+    for (int e = tid; e < d * d; e += nth) {
+        const int r = e / d, c = e % d;
+        const double* Lr = Lp + r * (r + 1) / 2;
+        const double* Lc = Lp + c * (c + 1) / 2;
+        double s = 0.0;
+        for (int p = 0; p <= (r < c ? r : c); ++p) s = fma(Lr[p], Lc[p], s);
+        out[e] = s;
+    }
+}
+
+__global__ void gen_steps_kernel(int64_t k, int n, int m, uint64_t seed, double f_scale, double* F,
+                                 double* H, double* K, double* G, double* C, double* o) {
+    extern __shared__ double sh[];
+    double* V = sh;                         // 3 x n reflection vectors
+    double* Q = sh + 3 * n;                 // f Q, n x n
+    double* Lp = Q + (size_t)n * n;         // packed lower factor
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int64_t nn = (int64_t)n * n;
+    for (int e = tid; e < 3 * n; e += nth) V[e] = gauss(seed, TAG_V, e);
+    __syncthreads();
+    double vv[3];
+    for (int j = 0; j < 3; ++j) {
+        vv[j] = 0.0;
+        for (int p = 0; p < n; ++p) vv[j] = fma(V[j * n + p], V[j * n + p], vv[j]);
+    }
+    for (int r = tid; r < n; r += nth) {
+        double* Qr = Q + (int64_t)r * n;
+        for (int p = 0; p < n; ++p) Qr[p] = (p == r) ? 1.0 : 0.0;
+        for (int j = 0; j < 3; ++j) {
+            const double* v = V + j * n;
+            double s = 0.0;
+            for (int p = 0; p < n; ++p) s = fma(Qr[p], v[p], s);
+            s *= 2.0 / vv[j];
+            for (int p = 0; p < n; ++p) Qr[p] = fma(-s, v[p], Qr[p]);
+        }
+        for (int p = 0; p < n; ++p) Qr[p] *= f_scale;
+    }
+    __syncthreads();
+    const double gs = sqrt(1.0 / n);
+    for (int64_t i = blockIdx.x; i < k; i += gridDim.x) {
+        if (i + 1 < k) {
+            for (int e = tid; e < n * n; e += nth) {
+                F[i * nn + e] = Q[e];
+                H[i * nn + e] = (e / n == e % n) ? 1.0 : 0.0;
+            }
+            gen_spd_into(K + i * nn, Lp, n, seed, TAG_LKS, TAG_DKS, (uint64_t)i * n);
+        }
+        if (m > 0) {
+            for (int e = tid; e < m * n; e += nth)
+                G[i * m * n + e] = gs * gauss(seed, TAG_GS, (uint64_t)i * m * n + e);
+            for (int e = tid; e < m; e += nth) o[i * m + e] = gauss(seed, TAG_O, (uint64_t)i * m + e);
+            gen_spd_into(C + i * (int64_t)m * m, Lp, m, seed, TAG_LCS, TAG_DCS, (uint64_t)i * m);
+        }
+    }
+}
+
+cudaError_t launch_generate_steps(int64_t k, int n, int m, uint64_t seed, double f_scale, double* F,
+                                  double* H, double* K, double* G, double* C, double* o,
+                                  cudaStream_t st) {
+    const int d = n > m ? n : m;
+    const size_t smem = sizeof(double) * (size_t)(3 * n + n * n + d * (d + 1) / 2);
+    if (smem > (size_t)SMEM_OPTIN_SM103) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(gen_steps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 4;
+    gen_steps_kernel<<<(unsigned)(k < cap ? k : cap), 128, smem, st>>>(k, n, m, seed, f_scale, F, H, K,
+                                                                         G, C, o);
+    ++t_launches;
     return cudaGetLastError();
 }
 

@@ -25,6 +25,8 @@ struct ks_fac {
     const SmallOps* small = nullptr;  // small-state path (element-major layouts) or generic
     void* R = nullptr;        // R store, k records of 3n^2+n elements (T)
     double* resid = nullptr;  // [2k]: residual parts of the level tiles and of the whitening
+    int var_N = 0;                // ks_smooth_var: padded dimension (0 = a uniform problem)
+    std::vector<int32_t> var_nd;  // ks_smooth_var: the caller's state dimensions n_i
 };
 
 struct ks_ctx {
@@ -55,6 +57,9 @@ struct ks_ctx {
     size_t bmeta_size = 0;
     std::map<std::string, cudaGraphExec_t> graphs;   // batch shape -> replayable launch graph
     std::set<std::string> shapes_seen;               // shapes already run once eagerly
+    // variable state dimensions (ks_smooth_var): offsets, padded inputs and outputs
+    void* vbuf = nullptr;
+    size_t vbuf_size = 0;
 };
 
 namespace kshost {

@@ -25,6 +25,9 @@ namespace ks {
 cudaError_t launch_generate(int64_t k, int n, int m, uint64_t seed, double f_scale, double* F,
                             double* H, double* K, double* G, double* C, double* o,
                             cudaStream_t st);
+cudaError_t launch_generate_steps(int64_t k, int n, int m, uint64_t seed, double f_scale, double* F,
+                                  double* H, double* K, double* G, double* C, double* o,
+                                  cudaStream_t st);
 }
 
 using namespace ks;
@@ -807,6 +810,17 @@ ks_status ks_generate(ks_ctx* ctx, int64_t k, int n, int m, uint64_t seed, doubl
     if (!ctx || k < 1 || n < 1 || m < 0 || !F || !H || !K || (m > 0 && (!G || !C || !o))) return KS_ERR_ARG;
     KS_CUDA(ctx, cudaSetDevice(ctx->device));
     KS_CUDA(ctx, launch_generate(k, n, m, seed, f_scale, F, H, K, G, C, o, ctx->stream));
+    if (ctx->sync) KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return KS_OK;
+}
+
+ks_status ks_generate_steps(ks_ctx* ctx, int64_t k, int n, int m, uint64_t seed, double f_scale,
+                            double* F, double* H, double* K, double* G, double* C, double* o) {
+    if (!ctx || k < 1 || n < 1 || m < 0 || (k > 1 && (!F || !H || !K)) ||
+        (m > 0 && (!G || !C || !o)))
+        return KS_ERR_ARG;
+    KS_CUDA(ctx, cudaSetDevice(ctx->device));
+    KS_CUDA(ctx, launch_generate_steps(k, n, m, seed, f_scale, F, H, K, G, C, o, ctx->stream));
     if (ctx->sync) KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return KS_OK;
 }

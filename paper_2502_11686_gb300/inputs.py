@@ -181,3 +181,91 @@ def uneven_batch(nprob: int = 512, seed0: int = 0, k_lo: int = 100, k_hi: int = 
         m = n if rng.uniform() < 0.5 else n // 2
         probs.append(random_problem(k, n, m, seed=seed0 + i, f_scale=0.99))
     return probs
+
+
+@dataclass
+class VarProblem:
+    """A problem whose state dimension varies from step to step (Section 2: u_i has n_i
+    entries; evolution equation i has l_i rows, H_i is l_i x n_{i+1} and F_i is l_i x n_i).
+
+    Packed row-major FP64 arrays in step order: F (l_i * n_i per equation), H (l_i * n_{i+1}),
+    c (l_i, or None), K (l_i * l_i), G (m_i * n_i per observation), o (m_i), C (m_i * m_i).
+    ``nd`` int32 [k] state dimensions, ``l`` int32 [k-1] evolution rows, ``m`` int32 [k]."""
+    k: int
+    nd: np.ndarray
+    l: np.ndarray
+    m: np.ndarray
+    F: np.ndarray
+    H: np.ndarray
+    c: np.ndarray | None
+    K: np.ndarray
+    G: np.ndarray
+    o: np.ndarray
+    C: np.ndarray
+    name: str = ""
+
+    def u_offsets(self):
+        off = np.zeros(self.k + 1, dtype=np.int64)
+        np.cumsum(self.nd.astype(np.int64), out=off[1:])
+        return off
+
+    def cov_offsets(self):
+        off = np.zeros(self.k + 1, dtype=np.int64)
+        np.cumsum(self.nd.astype(np.int64) ** 2, out=off[1:])
+        return off
+
+    def split_states(self, u):
+        off = self.u_offsets()
+        return [u[off[i]:off[i + 1]] for i in range(self.k)]
+
+    def split_cov(self, cov):
+        off = self.cov_offsets()
+        return [cov[off[i]:off[i + 1]].reshape(self.nd[i], self.nd[i]) for i in range(self.k)]
+
+
+def var_problem(k: int, ns=(3, 4, 6), seed: int = 0, rect: bool = True, m_mode: str = "n",
+                with_c: bool = True) -> VarProblem:
+    """Random problem with state dimension n_i drawn from ``ns`` per step.
+
+    l_i = n_{i+1} (square H_i) unless ``rect``, in which case l_i is drawn from
+    [max(1, n_{i+1} - 1), n_{i+1} + 1]: a dimension change handled by a rectangular H_i.
+    H_i = the l_i x n_{i+1} identity pattern plus N(0, 0.1^2) noise; F_i ~ N(0, 0.9^2 / n_i);
+    K_i, C_i = L L^T as in :func:`random_problem`; G_i ~ N(0, 1/n_i); o ~ N(0, 1).
+    ``m_mode``: "n" (m_i = n_i), "ragged" (m_i in {n_i - 1, n_i, n_i + 1}, m_0 = n_0), or
+    "gaps" (m_i = n_i, but one step in five has no observation; m_0 = n_0)."""
+    rng = np.random.default_rng(seed)
+    nd = rng.choice(np.asarray(ns), size=k).astype(np.int32)
+    if rect:
+        l = np.array([rng.integers(max(1, nd[i + 1] - 1), nd[i + 1] + 2) for i in range(k - 1)],
+                     dtype=np.int32)
+    else:
+        l = nd[1:].copy()
+    if m_mode == "n":
+        m = nd.copy()
+    elif m_mode == "ragged":
+        m = np.array([rng.integers(max(0, d - 1), d + 2) for d in nd], dtype=np.int32)
+        m[0] = nd[0]
+    else:
+        m = nd.copy()
+        m[1:][rng.uniform(size=k - 1) < 0.2] = 0
+    F, H, c, K, G, o, C = [], [], [], [], [], [], []
+    for i in range(k - 1):
+        li, ni, nj = int(l[i]), int(nd[i]), int(nd[i + 1])
+        F.append(rng.normal(0.0, 0.9 / np.sqrt(ni), size=(li, ni)).reshape(-1))
+        H.append((np.eye(li, nj) + rng.normal(0.0, 0.1, size=(li, nj))).reshape(-1))
+        K.append(random_spd(rng, 1, li).reshape(-1))
+        if with_c:
+            c.append(rng.normal(size=li))
+    for i in range(k):
+        mi, ni = int(m[i]), int(nd[i])
+        if mi:
+            G.append(rng.normal(0.0, np.sqrt(1.0 / ni), size=mi * ni))
+            o.append(rng.normal(size=mi))
+            C.append(random_spd(rng, 1, mi).reshape(-1))
+
+    def cat(parts):
+        return np.concatenate(parts) if parts else np.zeros(0)
+
+    return VarProblem(k=k, nd=nd, l=l, m=m, F=cat(F), H=cat(H), c=cat(c) if with_c else None,
+                      K=cat(K), G=cat(G), o=cat(o), C=cat(C),
+                      name=f"var k={k} ns={tuple(ns)} rect={rect} m={m_mode}")

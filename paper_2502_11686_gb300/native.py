@@ -27,7 +27,8 @@ EXPORTS = ("ks_default_options", "ks_create", "ks_smooth", "ks_covariances", "ks
            "ks_profile_read", "ks_smooth_static", "ks_smooth_batch", "ks_generate",
            "ks_server_create", "ks_server_submit", "ks_server_submit_synthetic",
            "ks_server_covariances", "ks_server_wait", "ks_server_result", "ks_server_release",
-           "ks_server_stats", "ks_server_destroy", "ks_measure_fma_rate")
+           "ks_server_stats", "ks_server_destroy", "ks_measure_fma_rate", "ks_smooth_var",
+           "ks_covariances_var", "ks_generate_steps")
 PHASES = ("whiten", "level", "backsub", "refine", "selinv", "copy", "batch")
 
 
@@ -127,6 +128,9 @@ def load():
         lib.ks_smooth_batch.restype = I
         lib.ks_generate.argtypes = [P, I64, I, I, ctypes.c_uint64, ctypes.c_double, P, P, P, P, P, P]
         lib.ks_generate.restype = I
+        lib.ks_generate_steps.argtypes = [P, I64, I, I, ctypes.c_uint64, ctypes.c_double, P, P, P,
+                                          P, P, P]
+        lib.ks_generate_steps.restype = I
         lib.ks_server_create.argtypes = [P, ctypes.POINTER(ks_server_options), ctypes.POINTER(P)]
         lib.ks_server_create.restype = I
         lib.ks_server_submit.argtypes = [P, ctypes.POINTER(ks_problem), ctypes.POINTER(I64)]
@@ -147,6 +151,11 @@ def load():
         lib.ks_server_destroy.restype = I
         lib.ks_measure_fma_rate.argtypes = [I, I, ctypes.POINTER(ctypes.c_double)]
         lib.ks_measure_fma_rate.restype = I
+        lib.ks_smooth_var.argtypes = [P, I64, P, P, P, P, P, P, P, P, P, P, P, ctypes.POINTER(P),
+                                      ctypes.POINTER(I64)]
+        lib.ks_smooth_var.restype = I
+        lib.ks_covariances_var.argtypes = [P, P, P]
+        lib.ks_covariances_var.restype = I
         _lib = lib
         return lib
 
@@ -272,6 +281,12 @@ def ks_generate(ctx, k, n, m, seed, f_scale, F, H, K, G, C, o):
     _check(ctx, st)
 
 
+def ks_generate_steps(ctx, k, n, m, seed, f_scale, F, H, K, G, C, o):
+    st = load().ks_generate_steps(ctx, int(k), int(n), int(m), int(seed), float(f_scale), ptr(F),
+                                  ptr(H), ptr(K), ptr(G), ptr(C), ptr(o))
+    _check(ctx, st)
+
+
 def ks_server_create(ctx, mem_budget=0, max_active=0, keep_factors=False):
     o = ks_server_options(int(mem_budget), int(max_active), 1 if keep_factors else 0)
     srv = ctypes.c_void_p()
@@ -360,3 +375,27 @@ def ks_measure_fma_rate(device, precision) -> float:
     if st != KS_OK:
         raise KsError(st, "ks_measure_fma_rate failed")
     return v.value
+
+
+def ks_smooth_var(ctx, k, nd, l, m, F, H, c, K, G, o, C, u_out, keep=False, check=True):
+    """Variable state dimensions (see include/ks.h).  nd, l, m: int32 host arrays.
+    Returns (status, handle or None, info)."""
+    import numpy as np
+    nd = np.ascontiguousarray(nd, dtype=np.int32)
+    lv = np.ascontiguousarray(l if l is not None and len(l) else np.zeros(1), dtype=np.int32)
+    m = np.ascontiguousarray(m, dtype=np.int32)
+    h = ctypes.c_void_p(None)
+    info = ctypes.c_int64(-1)
+    st = load().ks_smooth_var(ctx, int(k), ptr(nd), ptr(lv), ptr(m), ptr(F), ptr(H), ptr(c),
+                              ptr(K), ptr(G), ptr(o), ptr(C), ptr(u_out),
+                              ctypes.byref(h) if keep else None, ctypes.byref(info))
+    if check:
+        _check(ctx, st, info.value)
+    return st, (h if keep and h.value else None), info.value
+
+
+def ks_covariances_var(ctx, h, cov_out, check=True):
+    st = load().ks_covariances_var(ctx, h, ptr(cov_out))
+    if check:
+        _check(ctx, st)
+    return st

@@ -159,3 +159,60 @@ def rts_smoother(p):
         xs[i] = xf[i] + J @ (xs[i + 1] - xp[i + 1])
         Ps[i] = Pf[i] + J @ (Ps[i + 1] - Pp[i + 1]) @ J.T
     return np.array(xs), np.array(Ps)
+
+
+def dense_system_var(p):
+    """Whitened dense U A and U b of a problem with per-step state dimensions (``VarProblem``):
+    block column i has n_i columns; evolution equation i has l_i rows,
+    L_K^{-1} (H_i u_{i+1} - F_i u_i) = L_K^{-1} c_i with K_i = L_K L_K^T (Section 2)."""
+    k = p.k
+    uoff = p.u_offsets()
+    N = int(uoff[-1])
+    rows_A, rows_b = [], []
+    fo = ho = eo = ko = 0
+    go = gv = co = 0
+    for i in range(k):
+        ni, mi = int(p.nd[i]), int(p.m[i])
+        if mi:
+            Gi = p.G[gv:gv + mi * ni].reshape(mi, ni)
+            oi = p.o[go:go + mi]
+            Ci = p.C[co:co + mi * mi].reshape(mi, mi)
+            L = np.linalg.cholesky(Ci)
+            blk = np.zeros((mi, N))
+            blk[:, uoff[i]:uoff[i + 1]] = sla.solve_triangular(L, Gi, lower=True)
+            rows_A.append(blk)
+            rows_b.append(sla.solve_triangular(L, oi, lower=True))
+            go += mi
+            gv += mi * ni
+            co += mi * mi
+        if i + 1 < k:
+            li, nj = int(p.l[i]), int(p.nd[i + 1])
+            if li:
+                Fi = p.F[fo:fo + li * ni].reshape(li, ni)
+                Hi = p.H[ho:ho + li * nj].reshape(li, nj)
+                Ki = p.K[ko:ko + li * li].reshape(li, li)
+                ci = p.c[eo:eo + li] if p.c is not None else np.zeros(li)
+                L = np.linalg.cholesky(Ki)
+                blk = np.zeros((li, N))
+                blk[:, uoff[i]:uoff[i + 1]] = -sla.solve_triangular(L, Fi, lower=True)
+                blk[:, uoff[i + 1]:uoff[i + 2]] = sla.solve_triangular(L, Hi, lower=True)
+                rows_A.append(blk)
+                rows_b.append(sla.solve_triangular(L, ci, lower=True))
+            fo += li * ni
+            ho += li * nj
+            eo += li
+            ko += li * li
+    return np.vstack(rows_A), np.concatenate(rows_b)
+
+
+def dense_lstsq_var(p):
+    """States (packed) by dense least squares, covariance blocks (packed n_i x n_i) from the
+    explicit inverse of (UA)^T UA, and the minimal objective."""
+    A, b = dense_system_var(p)
+    x, *_ = np.linalg.lstsq(A, b, rcond=None)
+    Sinv = np.linalg.inv(A.T @ A)
+    uoff = p.u_offsets()
+    cov = np.concatenate([Sinv[uoff[i]:uoff[i + 1], uoff[i]:uoff[i + 1]].reshape(-1)
+                          for i in range(p.k)])
+    r = A @ x - b
+    return {"u": x, "cov": cov, "resid2": float(r @ r)}

@@ -123,7 +123,7 @@ def test_batch_fp32_refine():
         for (p, _), b in zip(problems, batch):
             ref = oracle.smooth(p)
             assert rel(to_np(b["u_out"]), ref["u"]) < 1e-6
-            assert rel_blocks(to_np(b["cov_out"]), ref["cov"]) < 1e-3
+            assert rel_blocks(to_np(b["cov_out"]), ref["cov"]) < 1e-5
 
 
 def test_batch_reports_failing_problem(sm64):

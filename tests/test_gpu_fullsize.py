@@ -20,7 +20,8 @@ from parity import TOL32_STATES, TOL64, check_blocks, check_states
 
 pytestmark = pytest.mark.gpu
 
-COV32 = {"n128": 1e-3, "n96": 1e-3}
+# about ten times the worst error measured on GB300: n128 2.3e-6 (lag-one blocks), n96 1.8e-6
+COV32 = {"n128": 3e-5, "n96": 2e-5}
 
 
 def run(precision, p, monkeypatch=None, no_tc=False):

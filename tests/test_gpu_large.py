@@ -11,6 +11,11 @@ import pytest
 
 import oracle
 from paper_2502_11686_gb300 import Smoother, inputs, native, problem_arrays
+from parity import TOL32_STATES, TOL64, check_blocks, check_states
+
+# FP32 covariance bound of the large-state path: about ten times the worst block error measured
+# at full size on GB300 (2.3e-6 at n = 128, k = 700).
+COV32 = 3e-5
 
 pytestmark = pytest.mark.gpu
 
@@ -43,12 +48,12 @@ def test_large_matches_oracle(n, k, precision):
         assert sm.max_n >= 128
         u, cov, r2 = run(sm, p)
     if precision == "fp64":
-        assert rel(u, ref["u"]) < 1e-10
-        assert rel_blocks(cov, ref["cov"]) < 1e-10
+        check_states(u, ref["u"], TOL64)
+        check_blocks(cov, ref["cov"], TOL64)
         assert abs(r2 - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"])
     else:
-        assert rel(u, ref["u"]) < 1e-6
-        assert rel_blocks(cov, ref["cov"]) < 1e-3
+        check_states(u, ref["u"], TOL32_STATES)
+        check_blocks(cov, ref["cov"], COV32)
 
 
 @pytest.mark.parametrize("n,k,m", [(72, 13, 72), (128, 9, 128), (100, 16, 61)])
@@ -64,10 +69,10 @@ def test_large_tensor_core_updates_match_cuda_cores(n, k, m, monkeypatch):
             out[flag] = run(sm, p)
     for flag in ("0", "1"):
         u, cov, _ = out[flag]
-        assert rel(u, ref["u"]) < 1e-6, flag
-        assert rel_blocks(cov, ref["cov"]) < 1e-3, flag
+        check_states(u, ref["u"], TOL32_STATES, f" KS_NO_TC={flag}")
+        check_blocks(cov, ref["cov"], COV32)
     assert rel(out["0"][0], out["1"][0]) < 1e-6
-    assert rel_blocks(out["0"][1], out["1"][1]) < 1e-3
+    assert rel_blocks(out["0"][1], out["1"][1]) < COV32
 
 
 def test_large_ragged_observations():
@@ -80,8 +85,8 @@ def test_large_ragged_observations():
     ref = oracle.smooth(p)
     with Smoother(device=0, precision="fp64") as sm:
         u, cov, _ = run(sm, p)
-    assert rel(u, ref["u"]) < 1e-10
-    assert rel_blocks(cov, ref["cov"]) < 1e-10
+    check_states(u, ref["u"], TOL64)
+    check_blocks(cov, ref["cov"], TOL64)
 
 
 def test_fp32_n64_full_observations():
@@ -90,8 +95,8 @@ def test_fp32_n64_full_observations():
     ref = oracle.smooth(p)
     with Smoother(device=0, precision="fp32_refine") as sm:
         u, cov, _ = run(sm, p)
-    assert rel(u, ref["u"]) < 1e-6
-    assert rel_blocks(cov, ref["cov"]) < 1e-3
+    check_states(u, ref["u"], TOL32_STATES)
+    check_blocks(cov, ref["cov"], COV32)
 
 
 def test_large_not_spd_reports_step():
@@ -122,8 +127,8 @@ def test_large_in_a_batch(precision):
         native.ks_smooth_batch(sm.ctx, batch)
     for p, b in zip(probs, batch):
         ref = oracle.smooth(p)
-        assert rel(b["u_out"].cpu().numpy(), ref["u"]) < tol, (p.k, p.n)
-        assert rel_blocks(b["cov_out"].cpu().numpy(), ref["cov"]) < (1e-10 if precision == "fp64" else 1e-3)
+        check_states(b["u_out"].cpu().numpy(), ref["u"], tol, f" k={p.k} n={p.n}")
+        check_blocks(b["cov_out"].cpu().numpy(), ref["cov"], TOL64 if precision == "fp64" else COV32)
 
 
 def test_large_served_request():
@@ -151,4 +156,4 @@ def test_large_served_request():
         cov_ref = sm.covariances(h, k, n, arr["F"])
         sm.release(h)
     assert rel(u.cpu().numpy(), u_ref.cpu().numpy()) < 1e-6
-    assert rel_blocks(cov.cpu().numpy(), cov_ref.cpu().numpy()) < 1e-3
+    assert rel_blocks(cov.cpu().numpy(), cov_ref.cpu().numpy()) < COV32

@@ -53,7 +53,7 @@ def test_med_kernel_matches_oracle_and_column_owner(n, k, precision, monkeypatch
         monkeypatch.setenv("KS_NO_MED", "1")
         u0, cov0, r20 = run(sm, p)
     tol_u = 1e-10 if precision == "fp64" else 1e-6
-    tol_c = 1e-10 if precision == "fp64" else 1e-3
+    tol_c = 1e-10 if precision == "fp64" else 1e-5
     assert rel(u, ref["u"]) < tol_u
     assert rel_blocks(cov, ref["cov"]) < tol_c
     assert rel(u, u0) < tol_u
@@ -78,7 +78,7 @@ def test_med_kernel_ragged_observations(n, precision, monkeypatch):
         monkeypatch.setenv("KS_NO_MED", "1")
         u0, cov0, _ = run(sm, p)
     tol_u = 1e-10 if precision == "fp64" else 1e-6
-    tol_c = 1e-10 if precision == "fp64" else 1e-3
+    tol_c = 1e-10 if precision == "fp64" else 1e-5
     assert rel(u, ref["u"]) < tol_u
     assert rel_blocks(cov, ref["cov"]) < tol_c
     assert rel(u, u0) < tol_u
@@ -98,6 +98,6 @@ def test_med_whitening_falls_back_for_wide_steps(precision):
     with Smoother(device=0, precision=precision) as sm:
         u, cov, r2 = run(sm, p)
     assert rel(u, ref["u"]) < (1e-10 if precision == "fp64" else 1e-6)
-    assert rel_blocks(cov, ref["cov"]) < (1e-10 if precision == "fp64" else 1e-3)
+    assert rel_blocks(cov, ref["cov"]) < (1e-10 if precision == "fp64" else 1e-5)
     if precision == "fp64":
         assert abs(r2 - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"])

@@ -14,8 +14,10 @@ from parity import TOL32_STATES, TOL64, check_blocks, check_states
 
 pytestmark = pytest.mark.gpu
 
-# FP32 covariance bounds per workload (worst covariance block, relative Frobenius error).
-COV32 = {"grid": 1e-5, "long_n6": 1e-5, "n48": 1e-4, "n16_m8": 1e-5}
+# FP32 covariance bounds per workload (worst covariance block, relative Frobenius error), about
+# ten times the worst error measured on GB300: grid 1.4e-6, long_n6 8.0e-7, n48 8.2e-7,
+# n16_m8 6.0e-7.
+COV32 = {"grid": 1e-5, "long_n6": 1e-5, "n48": 1e-5, "n16_m8": 1e-5}
 
 
 @pytest.fixture(scope="module")

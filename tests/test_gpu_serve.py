@@ -67,7 +67,10 @@ def problems():
 def test_each_result_same_alone_and_in_the_mix(precision):
     """Each request's result equals the same problem smoothed alone (and the oracle's), and the
     requests really ran together: some launches carried the work of several requests."""
-    probs = problems()
+    # A long request first: it is still working through its 17 levels when the waves arrive,
+    # so the waves' n = 6 requests share its level and back-substitution launches (each at its
+    # own recursion depth) whatever the speed of the ticks.
+    probs = [(inputs.random_problem(200_000, 6, 6, seed=2999, with_c=True), False)] + problems()
     tol = 1e-10 if precision == "fp64" else 1e-6
     with Smoother(device=0, precision=precision) as sm:
         refs = [alone(sm, p, c) for p, c in probs]
