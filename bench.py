@@ -31,8 +31,36 @@ sys.path.insert(0, ROOT)
 
 METRIC = "smoothed steps/s (FP64 plain vs FP32+refine batched) on 1 GB300; % roofline; p99 ms"
 UNIT = "steps/s"
-FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 peak is provided)
-FP32_PEAK_TFLOPS = 80.5      # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+# Nominal rates, quoted as context beside the measured ones (ks_measure_fma_rate).
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (recipe table)
+FP32_NOMINAL_TFLOPS = 80.5   # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+
+_PEAKS = {}
+
+
+def measured_peaks(device=0):
+    """FMA rates the device sustains, measured by the library (TFLOP/s): the denominators of
+    the arithmetic-bound rooflines."""
+    if not _PEAKS:
+        from paper_2502_11686_gb300 import native
+        _PEAKS["fp64"] = max(native.ks_measure_fma_rate(device, native.KS_FP64) for _ in range(2))
+        _PEAKS["fp32"] = max(native.ks_measure_fma_rate(device, native.KS_FP32_REFINE)
+                             for _ in range(2))
+    return _PEAKS
+
+
+def alu_roofline(kernel, flops, ms, fp64, device=0):
+    """Roofline record of an arithmetic-bound phase: algorithmic flops / its GPU time against
+    the measured FMA rate of its precision (nominal rate as context)."""
+    pk = measured_peaks(device)
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = pk["fp64"] if fp64 else pk["fp32"]
+    nominal = FP64_NOMINAL_TFLOPS if fp64 else FP32_NOMINAL_TFLOPS
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": ("measured DFMA rate of this GPU (ks_measure_fma_rate)" if fp64 else
+                            "measured FFMA rate of this GPU (ks_measure_fma_rate)"),
+            "peak_nominal": nominal, "frac_of_nominal": achieved / nominal, "traffic": None}
 
 WORKLOADS = {
     "long_k1e6_n6": dict(k=1_000_000, n=6, m=6, f_scale=0.99, sample_k=1_000_000,
@@ -220,52 +248,107 @@ def reference_arm(args, wl):
     return 0
 
 
-def batch_arm(args):
-    """The batched form: every step is one ks_smooth_batch call over resident inputs."""
+def _oracle_batch_task(task):
+    """Worker of the problem-parallel CPU baseline: one uneven-batch problem, drawn on the host
+    from its seed, smoothed by the oracle (states + covariances); returns (states, seconds)."""
+    seed, k_lo, k_hi, ns = task
+    import oracle
+    from paper_2502_11686_gb300 import inputs
+    k, n, m = inputs.uneven_shape(seed, k_lo, k_hi, ns)
+    p = inputs.random_problem(k, n, m, seed=seed, f_scale=0.99)
+    t0 = time.perf_counter()
+    oracle.smooth(p, covariances=True)
+    return k, time.perf_counter() - t0
+
+
+def oracle_pool():
+    """Process pool for the problem-parallel oracle: spawn (never fork after CUDA is up), one
+    worker per host core."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+def batch_cpu_baseline(wl, pool, cores, budget_s=12.0):
+    """The oracle on all host cores, problem-parallel (problems are independent), over the
+    first problems of the batch until about budget_s of wall time."""
+    tasks = [(i, wl["k_lo"], wl["k_hi"], wl["ns"]) for i in range(wl["nprob"])]
+    t0 = time.perf_counter()
+    steps, busy, done = 0, 0.0, 0
+    for k, sec in pool.imap_unordered(_oracle_batch_task, tasks):
+        steps += k
+        busy += sec
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    wall = time.perf_counter() - t0
+    return {"value": steps / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} problems of the batch recipe (same seeds, drawn on the host), "
+                      f"{steps} states + covariances, problem-parallel on {cores} host cores, "
+                      f"{wall:.1f} s wall ({busy:.1f} core-seconds in the oracle)"}
+
+
+def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, steps=None,
+                 warmup=None):
+    """The batched form (C4): every step is one ks_smooth_batch call over 512 resident problems
+    (states + covariances).  Inputs are drawn on the device (ks_generate_steps, the batch recipe
+    with the library's counter-based generator, problem i from seed i)."""
     import torch
 
-    import oracle
-    from paper_2502_11686_gb300 import inputs, native, problem_arrays
+    from paper_2502_11686_gb300 import inputs, native
 
-    wl = BATCH_WORKLOADS[args.workload]
-    nprob = args.nprob or wl["nprob"]
-    torch.cuda.set_device(0)
-    probs = inputs.uneven_batch(nprob, 0, wl["k_lo"], wl["k_hi"], wl["ns"])
-    total_k = sum(p.k for p in probs)
-    batch = []
-    for p in probs:
-        arr = problem_arrays(p, "cuda:0")
-        d = dict(arr, k=p.k, n=p.n, m=np.ascontiguousarray(p.m, dtype=np.int32),
-                 u_out=torch.empty((p.k, p.n), dtype=torch.float64, device="cuda:0"),
-                 cov_out=torch.empty((p.k, p.n, p.n), dtype=torch.float64, device="cuda:0"))
-        batch.append(d)
+    wl = dict(BATCH_WORKLOADS["batch_c4"], nprob=nprob)
+    steps = steps or args.steps
+    warmup = warmup or args.warmup
+    dev = "cuda:0"
+    shapes = [inputs.uneven_shape(i, wl["k_lo"], wl["k_hi"], wl["ns"]) for i in range(nprob)]
+    total_k = sum(k for k, _, _ in shapes)
     stream = torch.cuda.Stream()
-    prec = native.KS_FP64 if args.precision == "fp64" else native.KS_FP32_REFINE
+    prec = native.KS_FP64 if precision == "fp64" else native.KS_FP32_REFINE
 
     def make_ctx(profile):
         o = native.ks_default_options()
         o.precision = prec
         o.stream = stream.cuda_stream
         o.profile = 1 if profile else 0
+        o.sync = 0
         return native.ks_create(o)
 
+    gctx = make_ctx(False)
+    batch = []
+    in_bytes = 0
+    with torch.cuda.stream(stream):
+        for i, (k, n, m) in enumerate(shapes):
+            T = lambda *sh: torch.empty(sh, dtype=torch.float64, device=dev)   # noqa: E731
+            d = {"k": k, "n": n, "m": np.full(k, m, np.int32), "F": T(k - 1, n, n),
+                 "H": T(k - 1, n, n), "c": None, "K": T(k - 1, n, n), "G": T(k, m, n),
+                 "o": T(k, m), "C": T(k, m, m), "u_out": T(k, n), "cov_out": T(k, n, n)}
+            native.ks_generate_steps(gctx, k, n, m, i, 0.99, d["F"], d["H"], d["K"], d["G"],
+                                     d["C"], d["o"])
+            in_bytes += sum(d[x].numel() * 8 for x in ("F", "H", "K", "G", "o", "C")) + k * 4
+            batch.append(d)
+    native.ks_sync(gctx)
+    native.ks_destroy(gctx)
     ctx = make_ctx(False)
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             native.ks_smooth_batch(ctx, batch)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         with torch.cuda.stream(stream):
             ev0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 native.ks_smooth_batch(ctx, batch)
             ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
+    st, info = native.ks_sync(ctx)
+    if st != native.KS_OK:
+        raise native.KsError(st, native.ks_last_error(ctx), info)
     prof_graph = native.ks_profile_read(ctx)
     native.ks_destroy(ctx)
-    value = total_k * args.steps / (ms / 1e3)
+    value = total_k * steps / (ms / 1e3)
 
     # One profiled pass (launches issued one by one, each timed into its phase).
     pctx = make_ctx(True)
@@ -277,87 +360,87 @@ def batch_arm(args):
     native.ks_destroy(pctx)
     phase_ms = {k: v for k, v in prof["phase_ms"].items() if v > 0 and k != "copy"}
 
-    # The same problems one at a time in FP64 (ks_smooth + ks_covariances per problem).
-    o = native.ks_default_options()
-    o.stream = stream.cuda_stream
-    o.sync = 0
-    c64 = native.ks_create(o)
-    def per_problem():
-        for b in batch:
-            _, h, _ = native.ks_smooth(c64, b["k"], b["n"], b["m"], b["F"], b["H"], b["c"], b["K"],
-                                       b["G"], b["o"], b["C"], b["u_out"], keep=True)
-            native.ks_covariances(c64, h, b["cov_out"])
-            native.ks_release(c64, h)
-    with torch.cuda.stream(stream):
-        per_problem()
+    # End to end: the same call with pinned host arrays (the H2D copy of every input and the D2H
+    # copy of every state and covariance inside the timed region, every step).
+    e2e = None
+    if want_e2e:
+        hbatch = []
+        for d in batch:
+            h = dict(d)
+            for x in ("F", "H", "K", "G", "o", "C", "u_out", "cov_out"):
+                h[x] = torch.empty(d[x].shape, dtype=torch.float64).pin_memory()
+                if x not in ("u_out", "cov_out"):
+                    h[x].copy_(d[x])
+            hbatch.append(h)
+        ectx = make_ctx(False)
+        native.ks_smooth_batch(ectx, hbatch)
+        native.ks_sync(ectx)
+        e_steps = max(1, min(steps, 3))
         torch.cuda.synchronize()
-        ev0.record(stream)
-        per_problem()
-        ev1.record(stream)
-    torch.cuda.synchronize()
-    per_problem_fp64 = total_k / (ev0.elapsed_time(ev1) / 1e3)
-    native.ks_destroy(c64)
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            native.ks_smooth_batch(ectx, hbatch)
+        native.ks_sync(ectx)
+        torch.cuda.synchronize()
+        e_s = time.perf_counter() - t0
+        native.ks_destroy(ectx)
+        out_bytes = sum(d["u_out"].numel() * 8 + d["cov_out"].numel() * 8 for d in batch)
+        e2e = {"value": total_k * e_steps / e_s, "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
+               "d2h_bytes_per_step": int(out_bytes), "steps": e_steps,
+               "timing": "wall clock, device synchronized on both sides"}
+        del hbatch
 
-    # Roofline of the dominant phase: algorithmic flops summed over the problems.
     flops = {ph: 0.0 for ph in ("whiten", "level", "backsub", "selinv", "refine")}
-    for p in probs:
-        f = flops_per_step(p.n, int(p.m[0]), args.precision)
+    for k, n, m in shapes:
+        f = flops_per_step(n, m, precision)
         for ph in flops:
-            flops[ph] += f[ph] * p.k
+            flops[ph] += f[ph] * k
     top = max(flops, key=lambda ph: phase_ms.get(ph, 0.0))
-    achieved = flops[top] / (phase_ms[top] / 1e3) / 1e12
-    fp64_phase = args.precision == "fp64" or top in ("whiten", "refine")
-    peak = FP64_PEAK_TFLOPS if fp64_phase else FP32_PEAK_TFLOPS
-    roof = {"bound": "alu", "kernel": f"{top} phase (batched launches)", "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "peak_source": ("nominal FP64 rate of the GB300 (1.25 TFLOP/s)" if fp64_phase else
-                            "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
-            "traffic": None}
-    cpu = None
-    if not args.no_cpu_baseline:
-        t0, steps, i = time.perf_counter(), 0, 0
-        while time.perf_counter() - t0 < 10.0:
-            p = probs[i % len(probs)]
-            oracle.smooth(p)
-            steps += p.k
-            i += 1
-        el = time.perf_counter() - t0
-        cpu = {"value": steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the first {i} problems of the batch, one after another, states + "
-                         f"covariances, {el:.1f} s"}
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {wl['desc']}", "problems": nprob,
-                   "total_states": total_k, "precision": args.precision,
-                   "l2": "inputs larger than L2, no flush",
-                   "parallelism": "replicas only (independent problems)"},
-        "per_problem_fp64_steps_per_s": per_problem_fp64,
-        "roofline": roof, "phase_ms_per_step": phase_ms, "cpu_baseline": cpu, "e2e": None,
-        "gpu_launches": prof_graph["launches"] // max(1, args.steps + args.warmup) * args.steps,
+    fp64_phase = precision == "fp64" or top in ("whiten", "refine")
+    roof = alu_roofline(f"{top} phase (batched launches)", flops[top], phase_ms[top], fp64_phase)
+    cpu = batch_cpu_baseline(wl, pool, cores) if pool is not None else None
+    return {
+        "metric": "smoothed steps/s, batched", "value": value, "unit": UNIT,
+        "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
+        "dtype": "f64" if precision == "fp64" else "f32+f64",
+        "config": {"workload": f"batch_c4: {wl['desc']}", "problems": nprob,
+                   "total_states": total_k, "precision": precision,
+                   "inputs": "drawn on the device per problem seed (ks_generate_steps)",
+                   "l2": f"inputs ({in_bytes / 1e9:.1f} GB) larger than L2, no flush"},
+        "roofline": roof, "phase_ms_per_step": phase_ms, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": prof_graph["launches"] // max(1, steps + warmup) * steps,
         "clocks": clk.summary(),
     }
+
+
+def batch_arm(args):
+    pool, cores = oracle_pool() if not args.no_cpu_baseline else (None, 1)
+    rec = batch_record(args, args.nprob or BATCH_WORKLOADS[args.workload]["nprob"],
+                       args.precision, pool, cores, want_e2e=not args.no_e2e)
+    if pool is not None:
+        pool.terminate()
+    line = dict(rec, metric=METRIC, n_gpus=1, higher_is_better=True, scaling="weak",
+                vs_baseline=None, data="synthetic")
+    line["config"]["parallelism"] = "replicas only (independent problems)"
     print(json.dumps(line), flush=True)
     return 0
 
 
-def serve_arm(args):
+def serve_record(args, rates, duration, ns, precision, max_queue, verbose=True):
     """The serving loop: Poisson arrivals of synthetic requests (inputs generated on the device at
     admission), k log-uniform in [1e2, 1e5], n uniform over the served state sizes, m = n; 10 %
-    of the requests get a covariance follow-up on their kept factor.  Reports per offered rate the
-    completed throughput and the p50 / p99 latency from submission to completion."""
+    of the requests get a covariance follow-up on their kept factor.  Sweeps the offered rates
+    upward (stopping at the first saturated one) and reports, per rate, the completed throughput
+    and the p50 / p99 latency from submission to completion; the record's headline is the
+    highest rate that did not saturate."""
     import torch
 
     from paper_2502_11686_gb300 import native
 
     torch.cuda.set_device(0)
     o = native.ks_default_options()
-    o.precision = native.KS_FP64 if args.precision == "fp64" else native.KS_FP32_REFINE
+    o.precision = native.KS_FP64 if precision == "fp64" else native.KS_FP32_REFINE
     ctx = native.ks_create(o)
-    ns = [int(x) for x in args.serve_n.split(",")]
-    rates = [float(x) for x in args.rates.split(",")]
     results = []
     rng = np.random.default_rng(2024)
     seed = 0
@@ -398,9 +481,9 @@ def serve_arm(args):
         saturated = False
         while True:
             now = time.perf_counter()
-            if now - t0 >= args.duration:
+            if now - t0 >= duration:
                 break
-            if submitted % 8 == 0 and native.ks_server_stats(srv)["queued"] > args.max_queue:
+            if submitted % 8 == 0 and native.ks_server_stats(srv)["queued"] > max_queue:
                 saturated = True   # offered load above capacity: stop before the backlog grows
                 break
             if now < t_next:
@@ -421,8 +504,12 @@ def serve_arm(args):
         stats = native.ks_server_stats(srv)
         native.ks_server_destroy(srv)
         lat_a = np.array(lat)
+        # Every submitted request completes, so the served rate is window / (window + drain) of
+        # the offered one: a drain longer than 30 % of the window means the loop fell behind.
+        lagged = (total - submit_window) > 0.3 * submit_window
         results.append({
-            "offered_req_per_s": rate, "saturated": saturated, "submitted": submitted,
+            "offered_req_per_s": rate, "saturated": saturated or lagged,
+            "queue_overflow": saturated, "submitted": submitted,
             "completed": len(lat),
             "submit_window_s": submit_window, "drain_s": total - submit_window,
             "throughput_steps_per_s": done_steps / total,
@@ -432,20 +519,35 @@ def serve_arm(args):
             "p50_queue_ms": float(np.percentile(qms, 50)) if qms else None,
             "cov_followups": len(cov_lat),
             "p99_cov_ms": float(np.percentile(cov_lat, 99)) if cov_lat else None,
-            "ticks": stats["ticks"], "launches": stats["launches"]})
-        print(json.dumps({"serve_rate": results[-1]}), flush=True)
-        if saturated:
+            "ticks": stats["ticks"], "launches": stats["launches"],
+            "shared_launches": stats["shared_launches"],
+            "max_requests_per_launch": stats["max_requests_per_launch"]})
+        if verbose:
+            print(json.dumps({"serve_rate": results[-1]}), flush=True)
+        if saturated or lagged:
             break
     native.ks_destroy(ctx)
-    best = max(results, key=lambda r: r["throughput_steps_per_s"])
-    line = {"metric": METRIC, "value": best["throughput_steps_per_s"], "unit": UNIT, "n_gpus": 1,
-            "steps": len(rates), "warmup": 0, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+    ok = [r for r in results if not r["saturated"]] or results
+    best = max(ok, key=lambda r: r["offered_req_per_s"])
+    return {"metric": "served smoothed steps/s; p50 / p99 latency", "value":
+            best["throughput_steps_per_s"], "unit": UNIT,
+            "dtype": "f64" if precision == "fp64" else "f32+f64",
             "data": "synthetic (generated on the device at admission)",
             "config": {"workload": "serve: Poisson arrivals, k log-uniform [1e2, 1e5], n in "
                                    f"{ns}, m = n, 10 % covariance follow-ups",
-                       "precision": args.precision, "duration_s_per_rate": args.duration},
-            "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "rates": results}
+                       "precision": precision, "duration_s_per_rate": duration,
+                       "offered_req_per_s": best["offered_req_per_s"]},
+            "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
+            "saturated_at_req_per_s": next((r["offered_req_per_s"] for r in results
+                                            if r["saturated"]), None),
+            "rates": results}
+
+
+def serve_arm(args):
+    rec = serve_record(args, [float(x) for x in args.rates.split(",")], args.duration,
+                       [int(x) for x in args.serve_n.split(",")], args.precision, args.max_queue)
+    line = dict(rec, metric=METRIC, n_gpus=1, steps=len(rec["rates"]), warmup=0,
+                higher_is_better=True, scaling="weak", vs_baseline=None)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -472,6 +574,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--k", type=int, default=None,
                     help="override the number of states (smaller cases for profiling)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: leave out the batched and served records")
+    ap.add_argument("--batch-steps", type=int, default=3,
+                    help="default line: timed steps of the batched record")
+    ap.add_argument("--serve-rates", default="2,5,10",
+                    help="default line: offered rates (req/s) of the served record")
+    ap.add_argument("--serve-duration", type=float, default=5.0,
+                    help="default line: seconds of arrivals per rate of the served record")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -511,6 +621,12 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    extras = (world == 1 and not args.no_extras and args.workload == "long_k1e6_n6"
+              and args.k is None)
+    pool, cores = (None, 1)
+    if extras and not args.no_cpu_baseline:
+        pool, cores = oracle_pool()   # spawn: safe beside the CUDA context
 
     p = make_problem(wl, seed=rank)
     k, n = p.k, p.n
@@ -575,18 +691,19 @@ def main():
         e_steps = max(3, min(args.steps, 10))
         with torch.cuda.stream(stream):
             step(harr, hu, hc)
+            step(harr, hu, hc)
             native.ks_sync(ctx)
             barrier()
             torch.cuda.synchronize()
-            ev0.record(stream)
+            t0 = time.perf_counter()
             for _ in range(e_steps):
                 step(harr, hu, hc)
-            ev1.record(stream)
-        torch.cuda.synchronize()
-        st, info = native.ks_sync(ctx)
+            st, info = native.ks_sync(ctx)
+            torch.cuda.synchronize()
+            e_wall = time.perf_counter() - t0
         if st != native.KS_OK:
             raise native.KsError(st, native.ks_last_error(ctx), info)
-        e_ms = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device=f"cuda:{local}")
+        e_ms = torch.tensor([e_wall * 1e3], dtype=torch.float64, device=f"cuda:{local}")
         if world > 1:
             dist.all_reduce(e_ms, op=dist.ReduceOp.MAX)
         in_bytes = sum(int(v.numel() * v.element_size()) for nm, v in harr.items()
@@ -594,7 +711,9 @@ def main():
         e2e = {"value": world * k * e_steps / (float(e_ms.item()) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": in_bytes,
                "d2h_bytes_per_step": int(hu.numel() * 8 + hc.numel() * 8),
-               "steps": e_steps}
+               "steps": e_steps, "timing": "wall clock, device synchronized on both sides; "
+                                           "the input copy of a call overlaps the previous "
+                                           "call's kernels"}
         native.ks_profile_read(ctx, reset=True)
 
     if h is not None:
@@ -609,16 +728,10 @@ def main():
     by = bytes_per_step(n, m, args.precision)
     phase_ms = {ph: v / args.steps for ph, v in prof["phase_ms"].items() if v > 0}
     top = max(("whiten", "level", "backsub", "selinv", "refine"), key=lambda ph: phase_ms.get(ph, 0))
-    peak = FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS
-    achieved = fl[top] * k / (phase_ms[top] / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": f"{top} phase", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak,
-            "peak_source": ("nominal FP64 rate of the GB300 (1.25 TFLOP/s), no measured FP64 peak"
-                            if args.precision == "fp64" else
-                            "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"),
-            "flops_per_step": fl[top], "hbm_bytes_per_step": by[top],
-            "achieved_hbm_gbs": by[top] * k / (phase_ms[top] / 1e3) / 1e9,
-            "traffic": None}
+    fp64_phase = args.precision == "fp64" or top in ("whiten", "refine")
+    roof = alu_roofline(f"{top} phase", fl[top] * k, phase_ms[top], fp64_phase, local)
+    roof.update({"flops_per_step": fl[top], "hbm_bytes_per_step": by[top],
+                 "achieved_hbm_gbs": by[top] * k / (phase_ms[top] / 1e3) / 1e9})
     tr = measured_traffic(top, args.precision, n)
     if tr is not None and top == "level":
         launches = max(1, prof["phase_launches"]["level"] // args.steps)
@@ -653,6 +766,15 @@ def main():
         "gpu_launches": prof["launches"],
         "clocks": clk.summary(),
     }
+    if extras:
+        line["fp32_refine_batched"] = batch_record(args, BATCH_WORKLOADS["batch_c4"]["nprob"],
+                                                   "fp32_refine", pool, cores,
+                                                   steps=args.batch_steps, warmup=3)
+        line["serve"] = serve_record(args, [float(x) for x in args.serve_rates.split(",")],
+                                     args.serve_duration, [6, 24, 48, 128], "fp32_refine",
+                                     args.max_queue, verbose=False)
+    if pool is not None:
+        pool.terminate()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

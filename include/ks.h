@@ -156,6 +156,61 @@ ks_status ks_smooth_var(ks_ctx *ctx, int64_t k, const int32_t *nd, const int32_t
  * uncorrelated with the real ones and are dropped).  KS_ERR_ARG for a handle of ks_smooth. */
 ks_status ks_covariances_var(ks_ctx *ctx, ks_handle h, double *cov_out);
 
+/*
+ * Nonlinear smoothing (Section 2: with nonlinear evolution maps f_i and observation maps g_i the
+ * minimiser is found by a Gauss-Newton-type iteration, each step a LINEAR smoothing problem with
+ * the Jacobians at the current iterate, possibly concatenated with a diagonal matrix; only the
+ * states of those problems are needed).  Model: u_{i+1} = f_i(u_i) + eps_i (cov K_i, H_i = I),
+ * o_i = g_i(u_i) + delta_i (cov C_i, m rows at every step).
+ *
+ * ks_linearize_fn fills, for the iterate u (device, [k][n]), the device arrays
+ *   J [k-1][n][n] = df_i/du (u_i),   e [k-1][n] = f_i(u_i) - u_{i+1},
+ *   Gj [k][m][n] = dg_i/du (u_i),    r [k][m]   = o_i - g_i(u_i),
+ * with work ordered on `stream` (a cudaStream_t); it returns 0 on success.
+ */
+typedef int (*ks_linearize_fn)(void *user, int64_t k, int n, int m, const double *u, double *J,
+                               double *e, double *Gj, double *r, void *stream);
+
+typedef struct {
+    int max_iter;    /* most iterations (default 50) */
+    double lambda0;  /* initial Levenberg-Marquardt damping, > 0 (default 1e-3) */
+    double ftol;     /* stop after an accepted step that lowers the objective by <= ftol times
+                        its value (default 1e-12) */
+    double xtol;     /* stop when ||d|| <= xtol (||u|| + xtol) (default 1e-10) */
+} ks_gn_options;
+
+typedef struct {
+    int iterations, accepted, converged;  /* converged: stopped by ftol or xtol */
+    double objective0, objective;         /* Phi at the initial guess and at the result */
+    double lambda;                        /* final damping */
+} ks_gn_report;
+
+void ks_gn_default_options(ks_gn_options *opt);
+
+/*
+ * Levenberg-Marquardt from the initial guess in u (device [k][n]; overwritten by the result).
+ * Every iteration: damped observation blocks G'_i = [Gj_i ; I], o'_i = [r_i ; 0],
+ * C'_i = diag(C_i, I / lambda); the linear smoother (ks_smooth, the ctx's precision) for the
+ * correction d; the trial u + d is accepted if Phi = sum ||L_K,i^{-1} e_i||^2 +
+ * sum ||L_C,i^{-1} r_i||^2 decreases (lambda / 3), else rejected (4 lambda).  K [k-1][n][n] and
+ * C [k][m][m] are device arrays; 1 <= n <= 16, 0 <= m <= 16, k >= 2.  rep may be NULL.
+ * Returns the status of the first failing linear solve or callback, else KS_OK (also when
+ * max_iter ran out; see rep->converged).
+ */
+ks_status ks_gauss_newton(ks_ctx *ctx, int64_t k, int n, int m, ks_linearize_fn fn, void *user,
+                          const double *K, const double *C, double *u, const ks_gn_options *opt,
+                          ks_gn_report *rep);
+
+/* Built-in model for ks_gauss_newton: a pendulum, u = (theta, w), one symplectic Euler step
+ * w' = w - gravity sin(theta) dt, theta' = theta + w' dt; observation sin(theta) (n = 2,
+ * m = 1).  `user` points to a ks_pendulum whose o is the device array of the k observations. */
+typedef struct {
+    double dt, gravity;
+    const double *o;
+} ks_pendulum;
+int ks_pendulum_linearize(void *user, int64_t k, int n, int m, const double *u, double *J,
+                          double *e, double *Gj, double *r, void *stream);
+
 /* Bits of ks_problem.time_invariant: the array holds ONE matrix used at every step (a
  * time-invariant model) instead of one per step.  G and C may be time invariant only if every
  * m_i is the same. */

@@ -151,12 +151,12 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
                   {c, (size_t)(ke * n), false, 0},  {K, (size_t)(ke * nn), false, 0},
                   {G, (size_t)(tot_m * n), false, 0}, {o, (size_t)tot_m, false, 0},
                   {C, (size_t)tot_m2, false, 0}};
-    Plan plan;
+    Plan plan, splan;   // work memory; staging of host inputs
     const size_t o_lvlA = plan.take((size_t)k * CS * T);
     const size_t o_lvlB = plan.take((size_t)(k / 2 + 1) * CS * T);
     for (auto& s : src) {
         s.dev = s.p == nullptr || s.count == 0 || is_device_ptr(s.p);
-        if (!s.dev) s.off = plan.take(s.count * sizeof(double));
+        if (!s.dev) s.off = splan.take(s.count * sizeof(double));
     }
     const bool u_dev = is_device_ptr(u_out);
     const size_t o_u = u_dev ? 0 : plan.take((size_t)k * n * sizeof(double));
@@ -171,6 +171,8 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
         o_R = plan.take((size_t)k * RS * T);
         o_res = plan.take((size_t)2 * k * sizeof(double));
     }
+    const bool huge = n > LARGE_NMAX;   // factors of the whitening in per-block global slices
+    const size_t o_wscr = huge ? plan.take((size_t)huge_grid(k) * huge_whiten_scratch_bytes(n)) : 0;
     const size_t o_cn2 = plan.take((size_t)k * n * sizeof(double));
     const size_t o_cd2 = plan.take((size_t)k * n * sizeof(double));
     size_t o_LK = 0, o_LC = 0, o_g = 0, o_q = 0, o_w = 0, o_d = 0;
@@ -184,6 +186,13 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     }
     ks_status rs = reserve(ctx, plan.off);
     if (rs != KS_OK) return rs;
+    int ib = -1;   // input staging buffer of this call
+    if (splan.off > 0) {
+        ib = ctx->in_next;
+        rs = stage_reserve(ctx, ib, splan.off);
+        if (rs != KS_OK) return rs;
+        ctx->in_next ^= 1;
+    }
     char* ws = (char*)ctx->ws;
     cudaStream_t st = ctx->stream;
 
@@ -223,15 +232,21 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     std::vector<int64_t> goff, coff;
     {
     Phase ph_copy(ctx, KS_PHASE_COPY);
-    for (int i = 0; i < 7; ++i) {
-        if (src[i].dev) {
-            dptr[i] = src[i].p;
-        } else {
-            KS_CUDA(ctx, cudaMemcpyAsync(ws + src[i].off, src[i].p, src[i].count * sizeof(double),
-                                         cudaMemcpyHostToDevice, st));
-            dptr[i] = (const double*)(ws + src[i].off);
-        }
+    if (ib >= 0) {
+        // The copies wait only for the kernels of the call that last read this buffer (two calls
+        // back), not for the previous call, whose kernels they overlap.
+        ks_ctx::Stage& sb = ctx->in_stage[ib];
+        KS_CUDA(ctx, cudaStreamWaitEvent(ctx->cin, sb.free, 0));
+        for (int i = 0; i < 7; ++i)
+            if (!src[i].dev)
+                KS_CUDA(ctx, cudaMemcpyAsync((char*)sb.p + src[i].off, src[i].p,
+                                             src[i].count * sizeof(double), cudaMemcpyHostToDevice,
+                                             ctx->cin));
+        KS_CUDA(ctx, cudaEventRecord(sb.ready, ctx->cin));
+        KS_CUDA(ctx, cudaStreamWaitEvent(st, sb.ready, 0));
     }
+    for (int i = 0; i < 7; ++i)
+        dptr[i] = src[i].dev ? src[i].p : (const double*)((char*)ctx->in_stage[ib].p + src[i].off);
     if (!uniform) {
         goff.resize(k + 1);
         coff.resize(k + 1);
@@ -265,12 +280,16 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
     wa.cd2 = (double*)(ws + o_cd2);
     wa.bad = ctx->d_bad;
     wa.scratch = ws + o_lvlB;
+    wa.cta_scratch = huge ? ws + o_wscr : nullptr;
+    wa.cta_scratch_stride = huge ? (int64_t)huge_whiten_scratch_bytes(n) : 0;
     KS_CUDA(ctx, cudaMemsetAsync(resid, 0, (size_t)k * sizeof(double), st));
     {
         Phase ph(ctx, KS_PHASE_WHITEN);
         KS_CUDA(ctx, sops ? sops->whiten(wa, fp32, st) : launch_whiten(wa, fp32, st));
         KS_CUDA(ctx, launch_check_finite(wa, st));
     }
+    // FP64: nothing after the whitening reads the inputs, so the staging buffer is free.
+    if (ib >= 0 && !fp32) KS_CUDA(ctx, cudaEventRecord(ctx->in_stage[ib].free, st));
 
     // Odd-even levels.
     void* bufs[2] = {ws + o_lvlA, ws + o_lvlB};
@@ -325,6 +344,8 @@ ks_status ks_smooth(ks_ctx* ctx, int64_t k, int n, const int32_t* m, const doubl
         } else {
             KS_CUDA(ctx, launch_refine_warp(ra, (float*)ra.q, (float*)ra.g, (float*)w, (float*)d, R, L, st));
         }
+        // FP32 + refinement: the refinement re-reads the inputs; after it the buffer is free.
+        if (ib >= 0) KS_CUDA(ctx, cudaEventRecord(ctx->in_stage[ib].free, st));
     }
     if (!u_dev) {
         Phase ph(ctx, KS_PHASE_COPY);
@@ -358,6 +379,8 @@ ks_status ks_covariances(ks_ctx* ctx, ks_handle h, double* cov_out, double* cros
     const size_t T = fp32 ? 4 : 8;
     Plan plan;
     const size_t o_S = plan.take((size_t)k * 2 * nn * T);
+    const bool huge = n > LARGE_NMAX;   // Rd^{-1} of every block in a global slice
+    const size_t o_ri = huge ? plan.take((size_t)huge_grid((k + 1) / 2) * nn * T) : 0;
     const bool cov_dev = is_device_ptr(cov_out);
     const size_t o_cov = cov_dev ? 0 : plan.take((size_t)k * nn * sizeof(double));
     const bool cross_dev = cross_out == nullptr || is_device_ptr(cross_out);
@@ -377,7 +400,8 @@ ks_status ks_covariances(ks_ctx* ctx, ks_handle h, double* cov_out, double* cros
         const SmallOps* sops = h->small;
         for (int l = L; l >= 0; --l)
             KS_CUDA(ctx, sops ? sops->selinv(k, l, h->R, Sx, Sd, ctx->d_bad, fp32, st)
-                              : launch_selinv(n, k, l, h->R, Sx, Sd, ctx->d_bad, fp32, st));
+                         : huge ? launch_selinv_huge(n, k, l, h->R, Sx, Sd, ws + o_ri, ctx->d_bad, fp32, st)
+                                : launch_selinv(n, k, l, h->R, Sx, Sd, ctx->d_bad, fp32, st));
         if (cr) KS_CUDA(ctx, sops ? sops->cross(k, Sx, cr, fp32, st) : launch_cross(n, k, Sx, cr, fp32, st));
     }
     {
@@ -447,6 +471,7 @@ ks_status ks_destroy(ks_ctx* ctx) {
     ctx->graphs.clear();
     if (ctx->bmeta) cudaFree(ctx->bmeta);
     if (ctx->vbuf) cudaFree(ctx->vbuf);
+    if (ctx->gbuf) cudaFree(ctx->gbuf);
     for (ks_fac* f : ctx->facs) {
         cudaFree(f->R);
         cudaFree(f->resid);
@@ -454,6 +479,13 @@ ks_status ks_destroy(ks_ctx* ctx) {
     }
     ctx->facs.clear();
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->cin) cudaStreamSynchronize(ctx->cin);
+    for (auto& sb : ctx->in_stage) {
+        if (sb.p) cudaFree(sb.p);
+        if (sb.ready) cudaEventDestroy(sb.ready);
+        if (sb.free) cudaEventDestroy(sb.free);
+    }
+    if (ctx->cin) cudaStreamDestroy(ctx->cin);
     if (ctx->d_bad) cudaFree(ctx->d_bad);
     if (ctx->h_bad) cudaFreeHost(ctx->h_bad);
     if (ctx->h_scalar) cudaFreeHost(ctx->h_scalar);

@@ -97,7 +97,7 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
     KS_CUDA(ctx, cudaSetDevice(ctx->device));
     const bool fp32 = ctx->precision == KS_FP32_REFINE;
     const size_t T = fp32 ? 4 : 8;
-    const int maxn = max_n_for(ctx);
+    const int maxn = std::min(max_n_for(ctx), LARGE_NMAX);   // batched kernels stop at 128
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     load_tuning(ctx);

@@ -60,11 +60,26 @@ struct ks_ctx {
     // variable state dimensions (ks_smooth_var): offsets, padded inputs and outputs
     void* vbuf = nullptr;
     size_t vbuf_size = 0;
+    // Host inputs of ks_smooth are copied on `cin` into one of two staging buffers, so the copy
+    // for the next call runs while this call's kernels run.  `ready` (on cin) orders the
+    // kernels after the copy; `free` (on the ctx's stream, after the last kernel that reads the
+    // inputs) orders the copy of the call after next after them.
+    cudaStream_t cin = nullptr;
+    struct Stage {
+        void* p = nullptr;
+        size_t size = 0;
+        cudaEvent_t ready = nullptr, free = nullptr;
+    };
+    Stage in_stage[2];
+    int in_next = 0;
+    // ks_gauss_newton: linearizations, damped observation blocks, corrections
+    void* gbuf = nullptr;
+    size_t gbuf_size = 0;
 };
 
 namespace kshost {
 
-constexpr int KS_NMAX_API = LARGE_NMAX;
+constexpr int KS_NMAX_API = HUGE_NMAX;
 
 inline ks_status fail(ks_ctx* ctx, ks_status s, const char* fmt, ...) {
     if (ctx) {
@@ -109,7 +124,8 @@ struct Plan {
 
 inline ks_status reserve(ks_ctx* ctx, size_t bytes) {
     if (bytes <= ctx->ws_size) return KS_OK;
-    if (ctx->budget && bytes > ctx->budget)
+    const size_t staged = ctx->in_stage[0].size + ctx->in_stage[1].size;
+    if (ctx->budget && bytes + staged > ctx->budget)
         return fail(ctx, KS_ERR_OOM, "work memory %zu bytes exceeds the ctx budget %zu", bytes, ctx->budget);
     KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->ws) cudaFree(ctx->ws);
@@ -152,6 +168,27 @@ inline int max_m_for(const ks_ctx* ctx, int n) {
         if (m > best) best = m;
     }
     return best;
+}
+
+// Input staging buffer number `b` of at least `bytes` bytes, with its events and the copy
+// stream (created on first use).  Growing it waits for everything that may still use it.
+inline ks_status stage_reserve(ks_ctx* ctx, int b, size_t bytes) {
+    ks_ctx::Stage& s = ctx->in_stage[b];
+    if (!ctx->cin) KS_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cin, cudaStreamNonBlocking));
+    if (!s.ready) KS_CUDA(ctx, cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming));
+    if (!s.free) KS_CUDA(ctx, cudaEventCreateWithFlags(&s.free, cudaEventDisableTiming));
+    if (bytes <= s.size) return KS_OK;
+    size_t held = ctx->ws_size + ctx->in_stage[b ^ 1].size;
+    if (ctx->budget && held + bytes > ctx->budget)
+        return fail(ctx, KS_ERR_OOM, "staging %zu bytes of host inputs exceeds the ctx budget %zu", bytes, ctx->budget);
+    KS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    KS_CUDA(ctx, cudaStreamSynchronize(ctx->cin));
+    if (s.p) cudaFree(s.p);
+    s.p = nullptr;
+    s.size = 0;
+    KS_CUDA(ctx, cudaMalloc(&s.p, bytes));
+    s.size = bytes;
+    return KS_OK;
 }
 
 // Reads the device error words and resets them; returns the most severe code.

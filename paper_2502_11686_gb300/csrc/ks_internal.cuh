@@ -224,6 +224,8 @@ struct WhitenArgs {
     double* cd2;                  // out [k][n]: |D_{i-1} col|^2 (state i; row 0 = 0)
     unsigned long long* bad;
     void* scratch;                // large-state path: the second level buffer (free while whitening)
+    void* cta_scratch;            // state dimensions above 128: per-block slices (packed factors)
+    int64_t cta_scratch_stride;   //   bytes per block
 };
 
 // Numerical singularity test of a finished diagonal block of R: |R_ii| is compared with the
@@ -255,6 +257,15 @@ cudaError_t launch_check_finite(const WhitenArgs& a, cudaStream_t st);
 // dimensions the column-owner kernels cannot hold in shared memory, up to LARGE_NMAX, with
 // every m_i <= n.
 constexpr int LARGE_NMAX = 128;
+// Above LARGE_NMAX (up to HUGE_NMAX) the same kernels run with the QR panel in shared memory and
+// the Cholesky factors and Rd^{-1} in per-block slices of a global scratch (ks_smooth and
+// ks_covariances only; the batched and served forms stop at LARGE_NMAX).
+constexpr int HUGE_NMAX = 512;
+// Per-block scratch of the whitening (bytes) and the number of blocks it is sized for.
+size_t huge_whiten_scratch_bytes(int n);
+unsigned huge_grid(int64_t units);
+cudaError_t launch_selinv_huge(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
+                               void* ri_scratch, unsigned long long* bad, bool fp32, cudaStream_t st);
 __host__ __device__ __forceinline__ bool use_large(int n, bool fp32) { return fp32 ? n > 64 : n > 48; }
 size_t large_smem_bytes(int n, bool fp32);
 // Whether the column-owner whitening of (n, mmax) fits the opt-in shared memory of sm_103a;

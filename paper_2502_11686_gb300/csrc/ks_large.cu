@@ -618,6 +618,195 @@ __device__ void tpqrt_wy(int n, int p, const Blk<T>& F, const Blk<T>* C, int nc,
 }
 
 // ------------------------------------------------------------------------------------------
+// Blocked "triangle over full block" QR for full blocks of more than PMAX rows (state dimensions
+// above 128, up to BIG_NMAX).  The panel's reflectors stay in shared memory (p x PB); reflector
+// i is formed by one warp (norm by a shuffle reduction) and applied to the later panel columns
+// by all warps, a column per warp at a time; then the compact-WY factor T and the trailing
+// update of the remaining columns, BCW(T) columns at a time with the chunk of the full block
+// staged in shared memory:  W1 = Xt + V^T Xb,  W2 = T^T W1,  Xt -= W2,  Xb -= V W2.
+constexpr int BIG_NMAX = 512;
+template <typename T> struct BigCw { static constexpr int v = 32; };
+template <> struct BigCw<double> { static constexpr int v = 8; };
+
+template <typename T>
+struct BigSmem {
+    static constexpr int CW_ = BigCw<T>::v;
+    // offsets (elements of T) for full blocks of p rows
+    __host__ __device__ static int vs(int) { return 0; }
+    __host__ __device__ static int tp(int p) { return p * LDV; }
+    __host__ __device__ static int tm(int p) { return tp(p) + PB * LDV; }
+    __host__ __device__ static int yg(int p) { return tm(p) + PB * LDV; }
+    __host__ __device__ static int tau(int p) { return yg(p) + PB * LDV; }
+    __host__ __device__ static int xt(int p) { return tau(p) + PB; }
+    __host__ __device__ static int xb(int p) { return xt(p) + PB * CW_; }
+    __host__ __device__ static int w1(int p) { return xb(p) + p * CW_; }
+    __host__ __device__ static int w2(int p) { return w1(p) + PB * CW_; }
+    __host__ __device__ static int total(int p) { return w2(p) + PB * CW_; }
+    __host__ __device__ static size_t bytes(int p) { return (size_t)total(p) * sizeof(T); }
+};
+
+// Columns [c0, c0 + w) of block B by the panel (top rows kk0 .. kk0 + bw - 1).
+template <typename T>
+__device__ void big_apply_chunk(const Blk<T>& B, int c0, int w, int kk0, int bw, int p, T* sm) {
+    constexpr int CW_ = BigCw<T>::v;
+    const T* Vs = sm + BigSmem<T>::vs(p);
+    const T* Tm = sm + BigSmem<T>::tm(p);
+    T* Xt = sm + BigSmem<T>::xt(p);
+    T* Xb = sm + BigSmem<T>::xb(p);
+    T* W1 = sm + BigSmem<T>::w1(p);
+    T* W2 = sm + BigSmem<T>::w2(p);
+    const int tid = threadIdx.x;
+    for (int e = tid; e < PB * CW_; e += NTH) {
+        const int i = e / CW_, j = e - i * CW_;
+        Xt[e] = (i < bw && j < w) ? B.top[(int64_t)(kk0 + i) * B.ldt + c0 + j] : T(0);
+    }
+    for (int e = tid; e < p * CW_; e += NTH) {
+        const int r = e / CW_, j = e - r * CW_;
+        Xb[e] = j < w ? B.bot[(int64_t)r * B.ldb + c0 + j] : T(0);
+    }
+    __syncthreads();
+    // W1: PB x CW outputs over NTH threads, OUT consecutive columns each
+    constexpr int OUT = PB * CW_ / NTH;
+    static_assert(OUT >= 1 && CW_ % OUT == 0, "chunk width");
+    {
+        const int q = tid / (CW_ / OUT), j0 = (tid % (CW_ / OUT)) * OUT;
+        T acc[OUT];
+#pragma unroll
+        for (int o = 0; o < OUT; ++o) acc[o] = Xt[q * CW_ + j0 + o];
+        for (int r = 0; r < p; ++r) {
+            const T v = Vs[r * LDV + q];
+#pragma unroll
+            for (int o = 0; o < OUT; ++o) acc[o] = fma(v, Xb[r * CW_ + j0 + o], acc[o]);
+        }
+#pragma unroll
+        for (int o = 0; o < OUT; ++o) W1[q * CW_ + j0 + o] = acc[o];
+    }
+    __syncthreads();
+    {
+        const int q = tid / (CW_ / OUT), j0 = (tid % (CW_ / OUT)) * OUT;
+        T acc[OUT];
+#pragma unroll
+        for (int o = 0; o < OUT; ++o) acc[o] = T(0);
+        for (int s = 0; s <= q; ++s) {
+            const T tv = Tm[s * LDV + q];
+#pragma unroll
+            for (int o = 0; o < OUT; ++o) acc[o] = fma(tv, W1[s * CW_ + j0 + o], acc[o]);
+        }
+#pragma unroll
+        for (int o = 0; o < OUT; ++o) W2[q * CW_ + j0 + o] = acc[o];
+    }
+    __syncthreads();
+    for (int e = tid; e < bw * CW_; e += NTH) {
+        const int i = e / CW_, j = e - i * CW_;
+        if (j < w) B.top[(int64_t)(kk0 + i) * B.ldt + c0 + j] = Xt[e] - W2[e];
+    }
+    for (int e = tid; e < p * CW_; e += NTH) {
+        const int r = e / CW_, j = e - r * CW_;
+        if (j >= w) continue;
+        T a = Xb[e];
+        for (int s = 0; s < bw; ++s) a = fma(-Vs[r * LDV + s], W2[s * CW_ + j], a);
+        B.bot[(int64_t)r * B.ldb + c0 + j] = a;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void tpqrt_big(int n, int p, const Blk<T>& F, const Blk<T>* C, int nc, T* sm) {
+    constexpr int CW_ = BigCw<T>::v;
+    T* Vs = sm + BigSmem<T>::vs(p);
+    T* Tp = sm + BigSmem<T>::tp(p);
+    T* Tm = sm + BigSmem<T>::tm(p);
+    T* Y = sm + BigSmem<T>::yg(p);
+    T* tau_s = sm + BigSmem<T>::tau(p);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int NW = NTH / 32;
+    if (p == 0) return;
+    for (int kk0 = 0; kk0 < n; kk0 += PB) {
+        const int bw = n - kk0 < PB ? n - kk0 : PB;
+        __syncthreads();
+        for (int e = tid; e < p * PB; e += NTH) {
+            const int r = e / PB, j = e - r * PB;
+            Vs[r * LDV + j] = j < bw ? F.bot[(int64_t)r * F.ldb + kk0 + j] : T(0);
+        }
+        for (int e = tid; e < PB * PB; e += NTH) {
+            const int i = e / PB, j = e - i * PB;
+            Tp[i * LDV + j] = (i < bw && j < bw && i <= j) ? F.top[(int64_t)(kk0 + i) * F.ldt + kk0 + j] : T(0);
+        }
+        __syncthreads();
+        for (int i = 0; i < bw; ++i) {
+            // reflector i by warp 0: v = [1 ; x / (alpha - beta)], beta = -sign(alpha) |(alpha, x)|
+            if (warp == 0) {
+                T s = T(0);
+                for (int r = lane; r < p; r += 32) s = fma(Vs[r * LDV + i], Vs[r * LDV + i], s);
+                s = warp_sum(s);
+                const T alpha = Tp[i * LDV + i];
+                T g = T(0), tau = T(0), beta = alpha;
+                if (s != T(0)) {
+                    const T nrm = sqrt(fma(alpha, alpha, s));
+                    beta = alpha >= T(0) ? -nrm : nrm;
+                    g = T(1) / (alpha - beta);
+                    tau = (beta - alpha) / beta;
+                }
+                for (int r = lane; r < p; r += 32) Vs[r * LDV + i] *= g;
+                if (lane == 0) {
+                    Tp[i * LDV + i] = beta;
+                    tau_s[i] = tau;
+                }
+            }
+            __syncthreads();
+            const T tau = tau_s[i];
+            for (int j = i + 1 + warp; j < bw; j += NW) {
+                T d = T(0);
+                for (int r = lane; r < p; r += 32) d = fma(Vs[r * LDV + i], Vs[r * LDV + j], d);
+                d = warp_sum(d);
+                const T sc = tau * (d + Tp[i * LDV + j]);
+                for (int r = lane; r < p; r += 32) Vs[r * LDV + j] = fma(-sc, Vs[r * LDV + i], Vs[r * LDV + j]);
+                if (lane == 0) Tp[i * LDV + j] -= sc;
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < bw * bw; e += NTH) {
+            const int i = e / bw, j = e - i * bw;
+            if (i <= j) F.top[(int64_t)(kk0 + i) * F.ldt + kk0 + j] = Tp[i * LDV + j];
+        }
+        for (int e = tid; e < PB * PB; e += NTH) {
+            const int a = e / PB, b = e - a * PB;
+            T s = T(0);
+            if (a < b && b < bw)
+                for (int r = 0; r < p; ++r) s = fma(Vs[r * LDV + a], Vs[r * LDV + b], s);
+            Y[a * LDV + b] = s;
+        }
+        __syncthreads();
+        // T factor (warp 0; lane q owns row q):  T[i][i] = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] Y[0:i, i]
+        if (warp == 0) {
+            T* tq = Tm + lane * LDV;
+            for (int i = 0; i < PB; ++i) {
+                T a0 = T(0);
+                for (int s = lane; s < i; ++s) a0 = fma(tq[s], Y[s * LDV + i], a0);
+                const T ti = i < bw ? tau_s[i] : T(0);
+                tq[i] = lane < i ? -ti * a0 : (lane == i ? ti : T(0));
+            }
+        }
+        __syncthreads();
+        for (int c0 = kk0 + bw; c0 < n; c0 += CW_)
+            big_apply_chunk<T>(F, c0, (n - c0) < CW_ ? (n - c0) : CW_, kk0, bw, p, sm);
+        for (int b = 0; b < nc; ++b)
+            for (int c0 = 0; c0 < C[b].ncols; c0 += CW_)
+                big_apply_chunk<T>(C[b], c0, (C[b].ncols - c0) < CW_ ? (C[b].ncols - c0) : CW_, kk0, bw, p, sm);
+    }
+    __syncthreads();
+}
+
+// The QR of a level or whitening step: the register-panel form (with tensor cores in FP32) up
+// to PMAX rows, the shared-memory-panel form above.
+template <typename T>
+__device__ __forceinline__ void tpqrt_any(int n, int p, const Blk<T>& F, const Blk<T>* C, int nc,
+                                          T* sm, TcState* tc) {
+    if (n > PMAX) tpqrt_big<T>(n, p, F, C, nc, sm);
+    else tpqrt_wy<T>(n, p, F, C, nc, sm, tc);
+}
+
+// ------------------------------------------------------------------------------------------
 // Level tile t (records in the generic layout; see the file comment).
 template <typename T>
 __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* out, T* R,
@@ -651,7 +840,7 @@ __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* ou
     {
         const Blk<T> F{Rj, n, rec_E(rs), 2 * n, n};
         const Blk<T> C[2] = {{Rj + 2 * nn, n, rec_E(rs) + n, 2 * n, n}, {Rj + 3 * nn, 1, rec_RE(rs), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 2, sm, tc);
+        tpqrt_any<T>(n, n, F, C, 2, sm, tc);
     }
     if (j >= 1) {
         // step 2: [Rtilde_j ; D_j], companions [0 ; -B_j] (left), [X_j ; 0] (right), [t_j ; rE_j];
@@ -667,7 +856,7 @@ __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* ou
         const Blk<T> C[3] = {{Rj + nn, n, rec_E(ro), 2 * n, n},
                              {Rj + 2 * nn, n, rec_E(ro) + n, 2 * n, n},
                              {Rj + 3 * nn, 1, rec_RE(ro), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 3, sm, tc);
+        tpqrt_any<T>(n, n, F, C, 3, sm, tc);
     }
     for (int c = tid; c < n; c += NTH)
         if (diag_is_singular<T>(Rj[(int64_t)c * n + c], cn2[oj * n + c] + cd2[oj * n + c], n))
@@ -691,7 +880,7 @@ __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* ou
         __syncthreads();
         const Blk<T> F{Re, n, rec_E(re) + n, 2 * n, n};
         const Blk<T> C[2] = {{Re + nn, n, rec_E(re), 2 * n, n}, {Re + 3 * nn, 1, rec_RE(re), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 2, sm, tc);
+        tpqrt_any<T>(n, n, F, C, 2, sm, tc);
         for (int c = tid; c < n; c += NTH)
             if (diag_is_singular<T>(Re[(int64_t)c * n + c], cn2[oe * n + c] + cd2[oe * n + c], n))
                 flag_error(bad, ST_SINGULAR, oe);
@@ -702,12 +891,12 @@ __device__ void level_tile(int n, int64_t nc, int level, int64_t t, T* in, T* ou
     {
         const Blk<T> F{rec_C(ro), n, rec_E(rs) + n, 2 * n, n};
         const Blk<T> C[1] = {{rec_RC(ro), 1, rec_RE(rs), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 1, sm, tc);
+        tpqrt_any<T>(n, n, F, C, 1, sm, tc);
     }
     if (triple) {
         const Blk<T> F{rec_C(ro), n, rec_E(re), 2 * n, n};
         const Blk<T> C[1] = {{rec_RC(ro), 1, rec_RE(re), 1, 1}};
-        tpqrt_wy<T>(n, n, F, C, 1, sm, tc);
+        tpqrt_any<T>(n, n, F, C, 1, sm, tc);
     }
     if (threadIdx.x < 32) {
         double acc = 0.0;
@@ -854,7 +1043,11 @@ template <typename T>
 __device__ void whiten_step(const WhitenArgs& a, int64_t i, unsigned char* smem, TcState* tc = nullptr) {
     const int n = a.n, tid = threadIdx.x;
     const int64_t nn = (int64_t)n * n, CS = level_cs(n);
-    double* Lpk = reinterpret_cast<double*>(smem);
+    // Above PMAX the packed factors live in this block's slice of the global scratch (the shared
+    // memory holds the QR's panel); below, in shared memory.
+    double* Lpk = n > PMAX ? reinterpret_cast<double*>(reinterpret_cast<char*>(a.cta_scratch) +
+                                                       blockIdx.x * a.cta_scratch_stride)
+                           : reinterpret_cast<double*>(smem);
     const int tri = n * (n + 1) / 2;
     T* LT = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(Lpk) : reinterpret_cast<T*>(Lpk + tri);
     T* out = reinterpret_cast<T*>(a.level0);
@@ -901,6 +1094,8 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, unsigned char* smem,
         for (int col = tid; col < 2 * n; col += NTH) trsm_column<T>(LT, n, En + col, 2 * n);
         if (2 * n < NTH) {
             if (tid == 2 * n) trsm_column<T>(LT, n, REn, 1);
+        } else if (n > PMAX) {
+            if (tid == 0) trsm_column<T>(LT, n, REn, 1);
         } else if (tid < 32) {
             trsm_column_warp<T>(LT, n, REn);
         }
@@ -941,7 +1136,7 @@ __device__ void whiten_step(const WhitenArgs& a, int64_t i, unsigned char* smem,
         // [Chat_i | rC_i] = R of [0 ; L_C^{-1} [G_i | o_i]]
         const Blk<T> F{rec, n, Gm, n + 1, n};
         const Blk<T> C[1] = {{rec + nn, 1, Gm + n, n + 1, 1}};
-        tpqrt_wy<T>(n, mi, F, C, 1, reinterpret_cast<T*>(smem), tc);
+        tpqrt_any<T>(n, mi, F, C, 1, reinterpret_cast<T*>(smem), tc);
     }
     if (tid < 32) {
         double acc = 0.0;
@@ -1036,7 +1231,7 @@ __device__ void gemm_rows(int M, int N, int K, FA A, FB B, FK klo, FS st, T* As,
 // Row q of level `level`.  Sx row c = [Sl (n x n) | Sr (n x n)], Sd = covariances (FP64).
 template <typename T>
 __device__ void selinv_row(int n, int64_t k, int level, int64_t q, const T* __restrict__ R, T* Sx,
-                           double* Sd, unsigned long long* bad, T* sm) {
+                           double* Sd, unsigned long long* bad, T* sm, T* ri_global = nullptr) {
     const int tid = threadIdx.x;
     const int64_t nn = (int64_t)n * n;
     const int64_t c = ((2 * q + 1) << level) - 1;
@@ -1051,8 +1246,9 @@ __device__ void selinv_row(int n, int64_t k, int level, int64_t q, const T* __re
     const T* Rr = Rc + 2 * nn;
     T* Sl = Sx + c * 2 * nn;
     T* Sr = Sl + nn;
-    T* Ri = sm;
-    T* As = sm + nn;
+    // Rd^{-1}: in shared memory, or (state dimensions above PMAX) in this block's global scratch
+    T* Ri = ri_global ? ri_global : sm;
+    T* As = ri_global ? sm : sm + nn;
     T* Bs = As + GK * GM;
     double* slot = Sd + c * nn;
     // M and then S_cc share the FP64 covariance slot; in FP32 M sits in its second half so that
@@ -1153,11 +1349,12 @@ __global__ void __launch_bounds__(NTH) level_k(int n, int64_t nc, int level, T* 
 
 template <typename T>
 __global__ void __launch_bounds__(NTH) selinv_k(int n, int64_t k, int level, const T* R, T* Sx,
-                                                double* Sd, unsigned long long* bad) {
+                                                double* Sd, unsigned long long* bad, T* ri_scratch) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t rows = (k >> level) - (k >> (level + 1));
+    T* ri = ri_scratch ? ri_scratch + blockIdx.x * (int64_t)n * n : nullptr;
     for (int64_t q = blockIdx.x; q < rows; q += gridDim.x)
-        selinv_row<T>(n, k, level, q, R, Sx, Sd, bad, reinterpret_cast<T*>(smem_raw));
+        selinv_row<T>(n, k, level, q, R, Sx, Sd, bad, reinterpret_cast<T*>(smem_raw), ri);
 }
 
 template <typename T, int OP>
@@ -1237,6 +1434,11 @@ size_t with_tc(size_t base, bool fp32, int* off) {
 // region of the FP32 whitening and level kernels).
 size_t large_smem_bytes(int n, bool fp32) {
     using namespace large;
+    if (n > PMAX) {   // QR panel in shared memory; factors and Rd^{-1} in global scratch
+        const size_t q = fp32 ? BigSmem<float>::bytes(n) : BigSmem<double>::bytes(n);
+        const size_t sel = (size_t)(GK * GM + GK * GN) * (fp32 ? sizeof(float) : sizeof(double));
+        return q > sel ? q : sel;
+    }
     int off = -1;
     size_t m = with_tc(WhitenSmem::bytes(n, fp32), fp32, &off);
     const size_t q = with_tc(qr_bytes(fp32), fp32, &off);
@@ -1245,8 +1447,30 @@ size_t large_smem_bytes(int n, bool fp32) {
     return m;
 }
 
+size_t huge_whiten_scratch_bytes(int n) {
+    const size_t tri = (size_t)n * (n + 1) / 2;
+    return ((tri * sizeof(double) + tri * sizeof(float)) + 255) & ~(size_t)255;
+}
+
+unsigned huge_grid(int64_t units) { return large::grid_of(units, 1); }
+
 cudaError_t launch_whiten_large(const WhitenArgs& a, bool fp32, cudaStream_t st) {
     using namespace large;
+    if (a.n > PMAX) {   // one block per SM: its slice of a.cta_scratch holds the factors
+        if (a.cta_scratch == nullptr) return cudaErrorInvalidValue;
+        const unsigned grid = huge_grid(a.k);
+        if (fp32) {
+            const size_t smem = BigSmem<float>::bytes(a.n);
+            set_smem(whiten_k<float>, smem);
+            whiten_k<float><<<grid, NTH, smem, st>>>(a, -1);
+        } else {
+            const size_t smem = BigSmem<double>::bytes(a.n);
+            set_smem(whiten_k<double>, smem);
+            whiten_k<double><<<grid, NTH, smem, st>>>(a, -1);
+        }
+        ++t_launches;
+        return cudaGetLastError();
+    }
     int tc_off = -1;
     const size_t smem = with_tc(WhitenSmem::bytes(a.n, fp32), fp32, &tc_off);
     const unsigned grid = grid_of(a.k, tc_off >= 0 ? 1 : 2);
@@ -1266,6 +1490,20 @@ cudaError_t launch_level_large(int n, int64_t nc, int level, void* in, void* out
                                unsigned long long* bad, bool fp32, cudaStream_t st) {
     using namespace large;
     if (nc < 2) return cudaSuccess;
+    if (n > PMAX) {
+        const unsigned grid = grid_of(nc / 2, 1);
+        if (fp32) {
+            const size_t smem = BigSmem<float>::bytes(n);
+            set_smem(level_k<float>, smem);
+            level_k<float><<<grid, NTH, smem, st>>>(n, nc, level, (float*)in, (float*)out, (float*)R, resid, cn2, cd2, bad, -1, 0);
+        } else {
+            const size_t smem = BigSmem<double>::bytes(n);
+            set_smem(level_k<double>, smem);
+            level_k<double><<<grid, NTH, smem, st>>>(n, nc, level, (double*)in, (double*)out, (double*)R, resid, cn2, cd2, bad, -1, 0);
+        }
+        ++t_launches;
+        return cudaGetLastError();
+    }
     int tc_off = -1;
     const size_t smem = with_tc(qr_bytes(fp32), fp32, &tc_off);
     const unsigned grid = grid_of(nc / 2, tc_off >= 0 ? 1 : 2);
@@ -1290,10 +1528,31 @@ cudaError_t launch_selinv_large(int n, int64_t k, int level, const void* R, void
     const unsigned grid = grid_of(rows, fp32 ? 2 : 1);
     if (fp32) {
         set_smem(selinv_k<float>, smem);
-        selinv_k<float><<<grid, NTH, smem, st>>>(n, k, level, (const float*)R, (float*)Sx, Sd, bad);
+        selinv_k<float><<<grid, NTH, smem, st>>>(n, k, level, (const float*)R, (float*)Sx, Sd, bad, nullptr);
     } else {
         set_smem(selinv_k<double>, smem);
-        selinv_k<double><<<grid, NTH, smem, st>>>(n, k, level, (const double*)R, (double*)Sx, Sd, bad);
+        selinv_k<double><<<grid, NTH, smem, st>>>(n, k, level, (const double*)R, (double*)Sx, Sd, bad, nullptr);
+    }
+    ++t_launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_selinv_huge(int n, int64_t k, int level, const void* R, void* Sx, double* Sd,
+                               void* ri_scratch, unsigned long long* bad, bool fp32, cudaStream_t st) {
+    using namespace large;
+    const int64_t rows = (k >> level) - (k >> (level + 1));
+    if (rows <= 0) return cudaSuccess;
+    if (ri_scratch == nullptr) return cudaErrorInvalidValue;
+    const unsigned grid = huge_grid(rows);   // the scratch holds huge_grid(...) slices of n x n
+    const size_t smem = (size_t)(GK * GM + GK * GN) * (fp32 ? sizeof(float) : sizeof(double));
+    if (fp32) {
+        set_smem(selinv_k<float>, smem);
+        selinv_k<float><<<grid, NTH, smem, st>>>(n, k, level, (const float*)R, (float*)Sx, Sd, bad,
+                                                 (float*)ri_scratch);
+    } else {
+        set_smem(selinv_k<double>, smem);
+        selinv_k<double><<<grid, NTH, smem, st>>>(n, k, level, (const double*)R, (double*)Sx, Sd, bad,
+                                                  (double*)ri_scratch);
     }
     ++t_launches;
     return cudaGetLastError();

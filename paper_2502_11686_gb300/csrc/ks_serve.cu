@@ -551,7 +551,7 @@ Req* find_req(ks_server* S, int64_t id) {
 }
 
 ks_status fill_shape(ks_server* S, Req* r) {
-    const int maxn = max_n_for(S->ctx);
+    const int maxn = std::min(max_n_for(S->ctx), LARGE_NMAX);   // batched kernels stop at 128
     if (r->k < 1 || r->n < 1 || r->n > maxn) {
         S->err = "bad k or n";
         return KS_ERR_ARG;

@@ -286,7 +286,8 @@ static cudaError_t backsub_warp_nr(int n, int64_t k, int level, const void* R, b
 cudaError_t launch_backsub_warp(int n, int64_t k, int level, const void* R, bool fp32,
                                 double* u, cudaStream_t st) {
     return n <= 64 ? backsub_warp_nr<2>(n, k, level, R, fp32, u, st)
-                   : backsub_warp_nr<4>(n, k, level, R, fp32, u, st);
+           : n <= 128 ? backsub_warp_nr<4>(n, k, level, R, fp32, u, st)
+                      : backsub_warp_nr<16>(n, k, level, R, fp32, u, st);
 }
 
 template <int NR>
@@ -320,7 +321,8 @@ static cudaError_t refine_warp_nr(const RefineArgs& a, float* q, float* g, float
 cudaError_t launch_refine_warp(const RefineArgs& a, float* q, float* g, float* w, float* d,
                                const void* R, int L, cudaStream_t st) {
     return a.n <= 64 ? refine_warp_nr<2>(a, q, g, w, d, R, L, st)
-                     : refine_warp_nr<4>(a, q, g, w, d, R, L, st);
+           : a.n <= 128 ? refine_warp_nr<4>(a, q, g, w, d, R, L, st)
+                        : refine_warp_nr<16>(a, q, g, w, d, R, L, st);
 }
 
 // ---- batched column-owner launches ----------------------------------------------------------

@@ -175,12 +175,18 @@ def uneven_batch(nprob: int = 512, seed0: int = 0, k_lo: int = 100, k_hi: int = 
     n uniform over ``ns``, m = n/2 or n (equally likely)."""
     probs = []
     for i in range(nprob):
-        rng = np.random.default_rng(seed0 + i)
-        k = int(round(np.exp(rng.uniform(np.log(k_lo), np.log(k_hi)))))
-        n = int(rng.choice(ns))
-        m = n if rng.uniform() < 0.5 else n // 2
+        k, n, m = uneven_shape(seed0 + i, k_lo, k_hi, ns)
         probs.append(random_problem(k, n, m, seed=seed0 + i, f_scale=0.99))
     return probs
+
+
+def uneven_shape(seed: int, k_lo: int = 100, k_hi: int = 20000, ns=(4, 8, 16, 32)):
+    """(k, n, m) of the uneven-batch problem drawn from ``seed``."""
+    rng = np.random.default_rng(seed)
+    k = int(round(np.exp(rng.uniform(np.log(k_lo), np.log(k_hi)))))
+    n = int(rng.choice(ns))
+    m = n if rng.uniform() < 0.5 else n // 2
+    return k, n, m
 
 
 @dataclass
@@ -269,3 +275,43 @@ def var_problem(k: int, ns=(3, 4, 6), seed: int = 0, rect: bool = True, m_mode: 
     return VarProblem(k=k, nd=nd, l=l, m=m, F=cat(F), H=cat(H), c=cat(c) if with_c else None,
                       K=cat(K), G=cat(G), o=cat(o), C=cat(C),
                       name=f"var k={k} ns={tuple(ns)} rect={rect} m={m_mode}")
+
+
+@dataclass
+class PendulumProblem:
+    """Noisy observations of a simulated pendulum (the nonlinear-smoothing workload).
+
+    State u = (theta, w); the evolution is one symplectic Euler step, w' = w - g sin(theta) dt,
+    theta' = theta + w' dt, plus noise with covariance K = q [[dt^3/3, dt^2/2], [dt^2/2, dt]];
+    the observation sin(theta) plus noise with variance r.  ``K`` [k-1, 2, 2] and ``C`` [k, 1, 1] are stored per step,
+    ``o`` [k, 1]; ``u0`` is an initial guess built from the observations alone (theta =
+    arcsin of the clipped observation, w = its centred difference quotient)."""
+    k: int
+    dt: float
+    gravity: float
+    K: np.ndarray
+    C: np.ndarray
+    o: np.ndarray
+    truth: np.ndarray
+    u0: np.ndarray
+
+
+def pendulum_problem(k: int, seed: int = 0, dt: float = 0.01, q: float = 0.01, r: float = 0.01,
+                     gravity: float = 9.81, theta0: float = 1.2) -> PendulumProblem:
+    rng = np.random.default_rng(seed)
+    Q = q * np.array([[dt ** 3 / 3, dt ** 2 / 2], [dt ** 2 / 2, dt]])
+    Lq = np.linalg.cholesky(Q)
+    x = np.zeros((k, 2))
+    x[0] = (theta0, 0.0)
+    for i in range(1, k):
+        th, w = x[i - 1]
+        w1 = w - gravity * np.sin(th) * dt
+        x[i] = (th + w1 * dt, w1)
+        x[i] += Lq @ rng.normal(size=2)
+    o = np.sin(x[:, :1]) + np.sqrt(r) * rng.normal(size=(k, 1))
+    th = np.arcsin(np.clip(o[:, 0], -1.0, 1.0))
+    w = np.gradient(th, dt)
+    u0 = np.stack([th, w], axis=1)
+    return PendulumProblem(k=k, dt=dt, gravity=gravity,
+                           K=np.ascontiguousarray(np.broadcast_to(Q, (k - 1, 2, 2))),
+                           C=np.full((k, 1, 1), r), o=o, truth=x, u0=u0)

@@ -28,7 +28,8 @@ EXPORTS = ("ks_default_options", "ks_create", "ks_smooth", "ks_covariances", "ks
            "ks_server_create", "ks_server_submit", "ks_server_submit_synthetic",
            "ks_server_covariances", "ks_server_wait", "ks_server_result", "ks_server_release",
            "ks_server_stats", "ks_server_destroy", "ks_measure_fma_rate", "ks_smooth_var",
-           "ks_covariances_var", "ks_generate_steps")
+           "ks_covariances_var", "ks_generate_steps", "ks_gn_default_options",
+           "ks_gauss_newton", "ks_pendulum_linearize")
 PHASES = ("whiten", "level", "backsub", "refine", "selinv", "copy", "batch")
 
 
@@ -70,6 +71,26 @@ class ks_server_counters(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
                 ("bytes_budget", ctypes.c_size_t), ("shared_launches", ctypes.c_int64),
                 ("max_requests_per_launch", ctypes.c_int64)]
+
+
+class ks_gn_options(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("lambda0", ctypes.c_double), ("ftol", ctypes.c_double),
+                ("xtol", ctypes.c_double)]
+
+
+class ks_gn_report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("accepted", ctypes.c_int), ("converged", ctypes.c_int),
+                ("objective0", ctypes.c_double), ("objective", ctypes.c_double),
+                ("lambda_", ctypes.c_double)]
+
+
+class ks_pendulum(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("gravity", ctypes.c_double), ("o", ctypes.c_void_p)]
+
+
+LINEARIZE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class KsError(RuntimeError):
@@ -131,6 +152,13 @@ def load():
         lib.ks_generate_steps.argtypes = [P, I64, I, I, ctypes.c_uint64, ctypes.c_double, P, P, P,
                                           P, P, P]
         lib.ks_generate_steps.restype = I
+        lib.ks_gn_default_options.argtypes = [ctypes.POINTER(ks_gn_options)]
+        lib.ks_gn_default_options.restype = None
+        lib.ks_gauss_newton.argtypes = [P, I64, I, I, LINEARIZE_FN, P, P, P, P,
+                                        ctypes.POINTER(ks_gn_options), ctypes.POINTER(ks_gn_report)]
+        lib.ks_gauss_newton.restype = I
+        lib.ks_pendulum_linearize.argtypes = [P, I64, I, I, P, P, P, P, P, P]
+        lib.ks_pendulum_linearize.restype = ctypes.c_int
         lib.ks_server_create.argtypes = [P, ctypes.POINTER(ks_server_options), ctypes.POINTER(P)]
         lib.ks_server_create.restype = I
         lib.ks_server_submit.argtypes = [P, ctypes.POINTER(ks_problem), ctypes.POINTER(I64)]
@@ -399,3 +427,29 @@ def ks_covariances_var(ctx, h, cov_out, check=True):
     if check:
         _check(ctx, st)
     return st
+
+
+def ks_gn_default_options() -> ks_gn_options:
+    o = ks_gn_options()
+    load().ks_gn_default_options(ctypes.byref(o))
+    return o
+
+
+def pendulum_linearizer():
+    """The library's built-in pendulum linearization as a ks_linearize_fn pointer."""
+    return ctypes.cast(load().ks_pendulum_linearize, LINEARIZE_FN)
+
+
+def ks_gauss_newton(ctx, k, n, m, fn, user, K, C, u, opts=None, check=True):
+    """Levenberg-Marquardt smoothing (see include/ks.h).  fn: a LINEARIZE_FN (e.g.
+    pendulum_linearizer()); user: a ctypes object passed by reference (e.g. ks_pendulum).
+    Returns (status, report dict)."""
+    rep = ks_gn_report()
+    uptr = ctypes.addressof(user) if user is not None else None
+    st = load().ks_gauss_newton(ctx, int(k), int(n), int(m), fn, uptr, ptr(K), ptr(C), ptr(u),
+                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(rep))
+    if check:
+        _check(ctx, st)
+    return st, {"iterations": rep.iterations, "accepted": rep.accepted,
+                "converged": bool(rep.converged), "objective0": rep.objective0,
+                "objective": rep.objective, "lambda": rep.lambda_}

@@ -230,3 +230,33 @@ def test_synthetic_requests_match_ks_smooth(precision):
             assert rel(u.cpu().numpy(), u_ref.cpu().numpy()) < tol
             assert rel_blocks(cov.cpu().numpy(), cov_ref.cpu().numpy()) < (1e-10 if precision == "fp64" else 1e-3)
         native.ks_server_destroy(srv)
+
+
+def test_per_step_generator_recipe_and_parity():
+    """ks_generate_steps (the batched-benchmark inputs): F_i the same scaled orthogonal matrix at
+    every step, H_i = I, independent SPD K_i and C_i per step, G ~ N(0, 1/n), o ~ N(0, 1); and
+    the smoother on those very bytes matches the oracle."""
+    import torch
+    from inputs_helpers import as_problem
+    k, n, m = 3000, 8, 4
+    T = lambda *s: torch.empty(s, dtype=torch.float64, device="cuda")   # noqa: E731
+    F, H, K, G, C, o = T(k - 1, n, n), T(k - 1, n, n), T(k - 1, n, n), T(k, m, n), T(k, m, m), T(k, m)
+    with Smoother(device=0, precision="fp64") as sm:
+        native.ks_generate_steps(sm.ctx, k, n, m, 77, 0.99, F, H, K, G, C, o)
+        Fh, Kh, Ch = F.cpu().numpy(), K.cpu().numpy(), C.cpu().numpy()
+        assert np.array_equal(Fh, np.broadcast_to(Fh[0], Fh.shape))
+        assert np.allclose(Fh[0] @ Fh[0].T, 0.99 ** 2 * np.eye(n), atol=1e-12)
+        assert np.array_equal(H.cpu().numpy(), np.broadcast_to(np.eye(n), (k - 1, n, n)))
+        assert not np.array_equal(Kh[0], Kh[1]) and not np.array_equal(Ch[0], Ch[1])
+        assert np.allclose(Kh, np.swapaxes(Kh, 1, 2)) and np.all(np.linalg.eigvalsh(Kh) > 0)
+        assert np.all(np.linalg.eigvalsh(Ch) > 0)
+        assert abs(G.var().item() * n - 1.0) < 0.05 and abs(o.var().item() - 1.0) < 0.05
+        p = as_problem(k, n, m, F, H, K, G, C, o)
+        arr = {nm: getattr(p, nm) for nm in ("m", "F", "H", "c", "K", "G", "o", "C")}
+        u, h = sm.smooth(k, n, {x: (torch.from_numpy(v).cuda() if v is not None and x != "m" else v)
+                                for x, v in arr.items()}, keep=True)
+        cov = sm.covariances(h, k, n, F)
+        sm.release(h)
+    ref = oracle.smooth(p)
+    assert rel(u.cpu().numpy(), ref["u"]) < 1e-10
+    assert rel_blocks(cov.cpu().numpy(), ref["cov"]) < 1e-10
