@@ -76,6 +76,10 @@ WORKLOADS = {
     "large_k1e4_n128": dict(k=10_000, n=128, m=128, f_scale=0.995, sample_k=200, ref_sample_k=60,
                             desc="k=10,000 states, n=m=128, F=0.995*orth, H=I, G~N(0,1/128), "
                                  "K,C=LL^T per step; states + all covariances"),
+    "huge_k500_n500": dict(k=500, n=500, m=500, f_scale=0.995, sample_k=8, ref_sample_k=3,
+                           desc="k=500 states, n=m=500 (the paper's large-n regime), "
+                                "F=0.995*orth, H=I, G~N(0,1/500), K,C=LL^T per step; states + "
+                                "all covariances"),
 }
 
 

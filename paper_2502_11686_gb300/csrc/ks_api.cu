@@ -379,8 +379,8 @@ ks_status ks_covariances(ks_ctx* ctx, ks_handle h, double* cov_out, double* cros
     const size_t T = fp32 ? 4 : 8;
     Plan plan;
     const size_t o_S = plan.take((size_t)k * 2 * nn * T);
-    const bool huge = n > LARGE_NMAX;   // Rd^{-1} of every block in a global slice
-    const size_t o_ri = huge ? plan.take((size_t)huge_grid((k + 1) / 2) * nn * T) : 0;
+    const bool huge = n > LARGE_NMAX;   // Rd^{-1} and M of every block in a global slice
+    const size_t o_ri = huge ? plan.take((size_t)huge_grid((k + 1) / 2) * 2 * nn * T) : 0;
     const bool cov_dev = is_device_ptr(cov_out);
     const size_t o_cov = cov_dev ? 0 : plan.take((size_t)k * nn * sizeof(double));
     const bool cross_dev = cross_out == nullptr || is_device_ptr(cross_out);

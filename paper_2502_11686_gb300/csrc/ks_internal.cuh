@@ -258,7 +258,7 @@ cudaError_t launch_check_finite(const WhitenArgs& a, cudaStream_t st);
 // every m_i <= n.
 constexpr int LARGE_NMAX = 128;
 // Above LARGE_NMAX (up to HUGE_NMAX) the same kernels run with the QR panel in shared memory and
-// the Cholesky factors and Rd^{-1} in per-block slices of a global scratch (ks_smooth and
+// the Cholesky factors, Rd^{-1} and M of SelInv in per-block slices of a global scratch (ks_smooth and
 // ks_covariances only; the batched and served forms stop at LARGE_NMAX).
 constexpr int HUGE_NMAX = 512;
 // Per-block scratch of the whitening (bytes) and the number of blocks it is sized for.

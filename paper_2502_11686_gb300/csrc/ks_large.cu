@@ -1252,8 +1252,11 @@ __device__ void selinv_row(int n, int64_t k, int level, int64_t q, const T* __re
     T* Bs = As + GK * GM;
     double* slot = Sd + c * nn;
     // M and then S_cc share the FP64 covariance slot; in FP32 M sits in its second half so that
-    // writing row block I of S_cc (doubles) only overwrites rows of M already consumed.
-    T* Mx = sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(slot) : reinterpret_cast<T*>(slot) + nn;
+    // writing row block I of S_cc (doubles) only overwrites rows of M already consumed -- true
+    // while one 128-column tile covers a row block.  Above that (n > GN, where ri_global is
+    // given) M gets its own n x n after Rd^{-1} in the block's global slice.
+    T* Mx = ri_global ? ri_global + nn
+            : sizeof(T) == sizeof(double) ? reinterpret_cast<T*>(slot) : reinterpret_cast<T*>(slot) + nn;
 
     // Ri = Rd^{-1} (upper triangular), one thread per column.
     for (int64_t e = tid; e < nn; e += NTH) Ri[e] = T(0);
@@ -1352,7 +1355,7 @@ __global__ void __launch_bounds__(NTH) selinv_k(int n, int64_t k, int level, con
                                                 double* Sd, unsigned long long* bad, T* ri_scratch) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t rows = (k >> level) - (k >> (level + 1));
-    T* ri = ri_scratch ? ri_scratch + blockIdx.x * (int64_t)n * n : nullptr;
+    T* ri = ri_scratch ? ri_scratch + blockIdx.x * 2 * (int64_t)n * n : nullptr;   // Rd^{-1}, M
     for (int64_t q = blockIdx.x; q < rows; q += gridDim.x)
         selinv_row<T>(n, k, level, q, R, Sx, Sd, bad, reinterpret_cast<T*>(smem_raw), ri);
 }
@@ -1543,7 +1546,7 @@ cudaError_t launch_selinv_huge(int n, int64_t k, int level, const void* R, void*
     const int64_t rows = (k >> level) - (k >> (level + 1));
     if (rows <= 0) return cudaSuccess;
     if (ri_scratch == nullptr) return cudaErrorInvalidValue;
-    const unsigned grid = huge_grid(rows);   // the scratch holds huge_grid(...) slices of n x n
+    const unsigned grid = huge_grid(rows);   // the scratch holds huge_grid(...) slices of 2 n x n
     const size_t smem = (size_t)(GK * GM + GK * GN) * (fp32 ? sizeof(float) : sizeof(double));
     if (fp32) {
         set_smem(selinv_k<float>, smem);
