@@ -36,6 +36,12 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (recipe table)
 FP32_NOMINAL_TFLOPS = 80.5   # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 
 _PEAKS = {}
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress of the run on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench +{time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def measured_peaks(device=0):
@@ -318,6 +324,7 @@ def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, step
         o.sync = 0
         return native.ks_create(o)
 
+    log(f"batched record: drawing {nprob} problems ({total_k} states) on the device")
     gctx = make_ctx(False)
     batch = []
     in_bytes = 0
@@ -333,6 +340,7 @@ def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, step
             batch.append(d)
     native.ks_sync(gctx)
     native.ks_destroy(gctx)
+    log("batched record: warm-up (graph capture, grid tuning)")
     ctx = make_ctx(False)
     with torch.cuda.stream(stream):
         for _ in range(warmup):
@@ -354,6 +362,7 @@ def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, step
     native.ks_destroy(ctx)
     value = total_k * steps / (ms / 1e3)
 
+    log(f"batched record: {steps} timed passes, {ms / steps:.1f} ms each")
     # One profiled pass (launches issued one by one, each timed into its phase).
     pctx = make_ctx(True)
     with torch.cuda.stream(stream):
@@ -368,6 +377,7 @@ def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, step
     # copy of every state and covariance inside the timed region, every step).
     e2e = None
     if want_e2e:
+        log("batched record: pinned host copies of the inputs for the end-to-end pass")
         hbatch = []
         for d in batch:
             h = dict(d)
@@ -393,6 +403,7 @@ def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, step
                "d2h_bytes_per_step": int(out_bytes), "steps": e_steps,
                "timing": "wall clock, device synchronized on both sides"}
         del hbatch
+        log(f"batched record: end to end {e_s / e_steps * 1e3:.1f} ms per pass")
 
     flops = {ph: 0.0 for ph in ("whiten", "level", "backsub", "selinv", "refine")}
     for k, n, m in shapes:
@@ -402,7 +413,10 @@ def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, step
     top = max(flops, key=lambda ph: phase_ms.get(ph, 0.0))
     fp64_phase = precision == "fp64" or top in ("whiten", "refine")
     roof = alu_roofline(f"{top} phase (batched launches)", flops[top], phase_ms[top], fp64_phase)
-    cpu = batch_cpu_baseline(wl, pool, cores) if pool is not None else None
+    cpu = None
+    if pool is not None:
+        log(f"batched record: CPU baseline on {cores} host cores")
+        cpu = batch_cpu_baseline(wl, pool, cores)
     return {
         "metric": "smoothed steps/s, batched", "value": value, "unit": UNIT,
         "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
@@ -430,6 +444,9 @@ def batch_arm(args):
     return 0
 
 
+WAIT_LIMIT_MS = 120000.0   # requests still running this long after the last arrival are reported, not awaited
+
+
 def serve_record(args, rates, duration, ns, precision, max_queue, verbose=True):
     """The serving loop: Poisson arrivals of synthetic requests (inputs generated on the device at
     admission), k log-uniform in [1e2, 1e5], n uniform over the served state sizes, m = n; 10 %
@@ -455,27 +472,51 @@ def serve_record(args, rates, duration, ns, precision, max_queue, verbose=True):
         pending = []
         stop = threading.Event()
 
+        stuck = []
+        abort = threading.Event()
+
         def waiter():
+            # Polls every outstanding request (never blocks on one): a completed request is
+            # released at once, so its memory can admit the next one; a covariance follow-up is
+            # submitted when its request completes and awaited the same way.  Waiting on the
+            # requests one at a time could hold a finished request's memory while its
+            # predecessor's follow-up waits for memory.
             nonlocal done_steps
-            while not stop.is_set() or pending:
+            live = []   # [rid, k, follow, fid]
+            while not abort.is_set() and (not stop.is_set() or pending or live):
                 with lock:
-                    item = pending.pop(0) if pending else None
-                if item is None:
-                    time.sleep(0.0005)
-                    continue
-                rid, k, follow = item
-                info = native.ks_server_wait(srv, rid)
-                with lock:
-                    lat.append(info["latency_ms"])
-                    qms.append(info["queue_ms"])
-                    done_steps += k
-                if follow:
-                    fid = native.ks_server_covariances(srv, rid)
-                    finfo = native.ks_server_wait(srv, fid)
-                    with lock:
-                        cov_lat.append(finfo["latency_ms"])
-                    native.ks_server_release(srv, fid)
-                native.ks_server_release(srv, rid)
+                    while pending:
+                        live.append(list(pending.pop(0)) + [None])
+                still = []
+                for it in live:
+                    rid, k, follow, fid = it
+                    if fid is None:
+                        info = native.ks_server_wait(srv, rid, 0.0)
+                        if not info["done"]:
+                            still.append(it)
+                            continue
+                        with lock:
+                            lat.append(info["latency_ms"])
+                            qms.append(info["queue_ms"])
+                            done_steps += k
+                        if follow and info["status"] == native.KS_OK:
+                            it[3] = native.ks_server_covariances(srv, rid)
+                            still.append(it)
+                            continue
+                        native.ks_server_release(srv, rid)
+                    else:
+                        finfo = native.ks_server_wait(srv, fid, 0.0)
+                        if not finfo["done"]:
+                            still.append(it)
+                            continue
+                        with lock:
+                            cov_lat.append(finfo["latency_ms"])
+                        native.ks_server_release(srv, fid)
+                        native.ks_server_release(srv, rid)
+                live = still
+                time.sleep(0.0005)
+            if live:
+                stuck.append(live[0][0])
 
         th = threading.Thread(target=waiter, daemon=True)
         th.start()
@@ -485,7 +526,7 @@ def serve_record(args, rates, duration, ns, precision, max_queue, verbose=True):
         saturated = False
         while True:
             now = time.perf_counter()
-            if now - t0 >= duration:
+            if now - t0 >= duration or stuck:
                 break
             if submitted % 8 == 0 and native.ks_server_stats(srv)["queued"] > max_queue:
                 saturated = True   # offered load above capacity: stop before the backlog grows
@@ -502,8 +543,20 @@ def serve_record(args, rates, duration, ns, precision, max_queue, verbose=True):
             submitted += 1
             t_next += rng.exponential(1.0 / rate)
         submit_window = time.perf_counter() - t0
+        log(f"serve: {rate} req/s, {submitted} submitted in {submit_window:.1f} s; draining")
         stop.set()
-        th.join()
+        th.join(timeout=WAIT_LIMIT_MS / 1e3)
+        if th.is_alive():
+            abort.set()
+            th.join()
+        if stuck:
+            # A request did not complete within the limit: report it and leave the server (and
+            # its scheduler thread) alone rather than wait on it.
+            log(f"serve: request {stuck[0]} not done {WAIT_LIMIT_MS / 1e3:.0f} s after the last arrival")
+            return {"metric": "served smoothed steps/s; p50 / p99 latency", "value": None,
+                    "unit": UNIT, "error": f"request {stuck[0]} not complete "
+                                           f"{WAIT_LIMIT_MS / 1e3:.0f} s after the last arrival at "
+                                           f"{rate} req/s", "rates": results}
         total = time.perf_counter() - t0
         stats = native.ks_server_stats(srv)
         native.ks_server_destroy(srv)
@@ -654,6 +707,7 @@ def main():
                                    a["o"], a["C"], uo, keep=True, reuse=h)
         native.ks_covariances(ctx, h, co)
 
+    log(f"{args.workload}: {args.warmup} warm-up passes")
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step(arr, u, cov)
@@ -682,6 +736,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     value = world * k * args.steps / (ms_max / 1e3)
+    log(f"{args.workload}: {args.steps} timed passes, {ms_max / args.steps:.3f} ms each")
 
     # End to end through the same C ABI with pinned host buffers: every step copies its
     # inputs in and its states and covariances out inside the timed region.
@@ -719,6 +774,7 @@ def main():
                                            "the input copy of a call overlaps the previous "
                                            "call's kernels"}
         native.ks_profile_read(ctx, reset=True)
+        log(f"{args.workload}: end to end {e_wall * 1e3 / e_steps:.3f} ms per pass")
 
     if h is not None:
         native.ks_release(ctx, h)
@@ -745,6 +801,7 @@ def main():
         roof["algorithmic_bytes_per_launch"] = by[top] * k / launches
     cpu = None
     if not args.no_cpu_baseline and world == 1:
+        log(f"{args.workload}: CPU baseline (oracle, 1 host core)")
         rate, sample = oracle_rate(wl)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     try:
@@ -774,6 +831,7 @@ def main():
         line["fp32_refine_batched"] = batch_record(args, BATCH_WORKLOADS["batch_c4"]["nprob"],
                                                    "fp32_refine", pool, cores,
                                                    steps=args.batch_steps, warmup=3)
+        log("served record")
         line["serve"] = serve_record(args, [float(x) for x in args.serve_rates.split(",")],
                                      args.serve_duration, [6, 24, 48, 128], "fp32_refine",
                                      args.max_queue, verbose=False)

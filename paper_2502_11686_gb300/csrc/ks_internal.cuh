@@ -228,6 +228,18 @@ struct WhitenArgs {
     int64_t cta_scratch_stride;   //   bytes per block
 };
 
+// Smallest normal number of T.  The reflector kernels that form tau and 1 / (alpha - beta) from
+// the single reciprocal 1 / (beta (alpha - beta)) treat a column with alpha^2 + |x|^2 below it as
+// zero: that product would be subnormal and its reciprocal overflow.  (In a rank-deficient block
+// the columns past its rank keep rounding-level tails that shrink by a factor of about eps per
+// reflector, so they reach that range after a few columns.)
+template <typename T>
+__host__ __device__ __forceinline__ T tiny_normal();
+template <>
+__host__ __device__ __forceinline__ double tiny_normal<double>() { return 2.2250738585072014e-308; }
+template <>
+__host__ __device__ __forceinline__ float tiny_normal<float>() { return 1.17549435e-38f; }
+
 // Numerical singularity test of a finished diagonal block of R: |R_ii| is compared with the
 // 2-norm of column i of the whitened matrix U A for that state (orthogonal transformations
 // keep column norms, so |R_ii| <= that norm, and a ratio at rounding level means the column is

@@ -73,10 +73,11 @@ __device__ __forceinline__ void med_tpqrt(T (&top)[N], T (&bot)[N], int fcol, bo
         if (fcol == kk) {
             const T alpha = top[kk];
             const T sigma = norm2;
-            const T nrm = msqrt<T>(fma(alpha, alpha, sigma));
+            const T s2 = fma(alpha, alpha, sigma);
+            const T nrm = msqrt<T>(s2);
             const T beta = alpha >= T(0) ? -nrm : nrm;
             const T d = alpha - beta;
-            const bool ok = sigma != T(0);
+            const bool ok = sigma != T(0) && s2 >= tiny_normal<T>();
             const T r = T(1) / (beta * d);
             const T g = ok ? beta * r : T(0);
             sm[S::TAU] = ok ? -(d * d) * r : T(0);
@@ -411,10 +412,11 @@ __device__ __forceinline__ void med_geqr(T (&x)[N], int fcol, bool active, int m
         const bool live = kk < m;   // reflectors past m are identities; barriers stay uniform
         if (live && fcol == kk) {
             const T alpha = x[kk];
-            const T nrm = msqrt<T>(fma(alpha, alpha, sig));
+            const T s2 = fma(alpha, alpha, sig);
+            const T nrm = msqrt<T>(s2);
             const T beta = alpha >= T(0) ? -nrm : nrm;
             const T d = alpha - beta;
-            const bool ok = sig != T(0);
+            const bool ok = sig != T(0) && s2 >= tiny_normal<T>();
             const T r = T(1) / (beta * d);
             const T g = ok ? beta * r : T(0);
             *tau_s = ok ? -(d * d) * r : T(0);

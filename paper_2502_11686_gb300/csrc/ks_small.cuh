@@ -61,7 +61,8 @@ struct RowView {
 
 // ---- Householder QR of [T ; M] in registers (T: N x N upper triangular, M: P x N) ----------
 // Same reflector convention as the column-owner kernels: beta = -sign(alpha) |[alpha; x]|,
-// tau = (beta - alpha) / beta, v = [1 ; x / (alpha - beta)], zero x -> no reflection.  The
+// tau = (beta - alpha) / beta, v = [1 ; x / (alpha - beta)], zero x (or alpha^2 + |x|^2 below
+// the smallest normal number) -> no reflection.  The
 // scaled tail x / (alpha - beta) is stored in place of x, so applying H to [a ; b] is
 //   s = tau (a_kk + v . b),  a_kk -= s,  b -= s v.
 template <typename T, int N, int P>
@@ -72,10 +73,11 @@ __device__ __forceinline__ void reg_factor(T (&Tm)[N][N], T (&M)[P][N], T (&tau)
         T sigma = T(0);
 #pragma unroll
         for (int i = 0; i < P; ++i) sigma = fma(M[i][kk], M[i][kk], sigma);
-        const T nrm = sqrt(fma(alpha, alpha, sigma));
+        const T s2 = fma(alpha, alpha, sigma);
+        const T nrm = sqrt(s2);
         const T beta = alpha >= T(0) ? -nrm : nrm;
         const T d = alpha - beta;
-        const bool ok = sigma != T(0);
+        const bool ok = sigma != T(0) && s2 >= tiny_normal<T>();
         const T r = T(1) / (beta * d);   // one reciprocal gives both tau and 1 / (alpha - beta)
         const T g = ok ? beta * r : T(0);
         const T ta = ok ? -(d * d) * r : T(0);

@@ -5,7 +5,8 @@ blocks of the large-state level kernel (one block per SM while it holds the tens
 works through two or three tiles, and the in-place records no longer fit in L2 at once; the
 tensor-core chunk loop runs exactly as in the benchmarked workload.  The same inputs are
 smoothed in FP64, in FP32 + refinement with the tcgen05 trailing updates, and with the CUDA-core
-updates (KS_NO_TC=1), each against one oracle run: states (global and per state), every
+updates (KS_NO_TC=1), and with the tensor-core kernel at two blocks per SM taking turns on the
+tensor memory (KS_TC_BLOCKS=2), each against one oracle run: states (global and per state), every
 covariance block and every lag-one block.  Also: n = 96 with ragged observation counts
 (including steps without observations), FP64 n = 48 at k = 5000 (m = 48 and m = 24), and the
 lag-one blocks of the register-column path (n = 16).
@@ -24,9 +25,10 @@ pytestmark = pytest.mark.gpu
 COV32 = {"n128": 3e-5, "n96": 2e-5}
 
 
-def run(precision, p, monkeypatch=None, no_tc=False):
+def run(precision, p, monkeypatch=None, no_tc=False, tc_blocks=1):
     if monkeypatch is not None:
         monkeypatch.setenv("KS_NO_TC", "1" if no_tc else "0")
+        monkeypatch.setenv("KS_TC_BLOCKS", str(tc_blocks))
     with Smoother(device=0, precision=precision) as sm:
         arr = problem_arrays(p, "cuda")
         u, h = sm.smooth(p.k, p.n, arr, keep=True)
@@ -51,10 +53,11 @@ def test_n128_fp64_full_size(n128):
     assert abs(r2 - ref["resid2"]) <= 1e-9 * max(1.0, ref["resid2"])
 
 
-@pytest.mark.parametrize("no_tc", [False, True], ids=["tcgen05", "cuda_cores"])
-def test_n128_fp32_refine_full_size(n128, no_tc, monkeypatch):
+@pytest.mark.parametrize("no_tc,tc_blocks", [(False, 1), (False, 2), (True, 1)],
+                         ids=["tcgen05", "tcgen05_two_blocks_per_sm", "cuda_cores"])
+def test_n128_fp32_refine_full_size(n128, no_tc, tc_blocks, monkeypatch):
     p, ref = n128
-    u, cov, cross, _ = run("fp32_refine", p, monkeypatch, no_tc)
+    u, cov, cross, _ = run("fp32_refine", p, monkeypatch, no_tc, tc_blocks)
     check_states(u, ref["u"], TOL32_STATES)
     check_blocks(cov, ref["cov"], COV32["n128"])
     check_blocks(cross, ref["cross"], COV32["n128"], "cross")

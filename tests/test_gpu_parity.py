@@ -211,3 +211,21 @@ def test_refine_workloads(sm32, n, m, k, cls):
     got = run(sm32, p)
     check_states(got["u"], ref["u"], TOL32_STATES)
     check_blocks(got["cov"], ref["cov"], COV32[cls])
+
+
+@pytest.mark.parametrize("n,m,precision", [(8, 2, "fp32_refine"), (8, 1, "fp32_refine"),
+                                           (16, 2, "fp32_refine"), (6, 1, "fp64"),
+                                           (8, 2, "fp64"), (16, 3, "fp64")])
+def test_rank_deficient_observation_blocks(n, m, precision, sm64, sm32):
+    """Observation blocks of rank m < n: the whitening's QR meets columns whose tails are only
+    rounding residue, shrinking by about eps per reflector; such a column must be taken as zero
+    once alpha^2 + |x|^2 drops below the smallest normal number, not divided by."""
+    p = inputs.random_problem(400, n, m, seed=400 + 10 * n + m, with_c=True, f_scale=0.99)
+    ref = oracle.smooth(p, covariances=True)
+    out = run(sm64 if precision == "fp64" else sm32, p)
+    if precision == "fp64":
+        check_states(out["u"], ref["u"], TOL64)
+        check_blocks(out["cov"], ref["cov"], TOL64)
+    else:
+        check_states(out["u"], ref["u"], TOL32_STATES)
+        check_blocks(out["cov"], ref["cov"], COV32["grid"])
