@@ -362,13 +362,14 @@ __device__ __forceinline__ void tc_epi1_part(const float (&v)[32], const float (
 
 // Trailing update of the chunk's columns by the panel whose reflectors are rows kk0 .. kk0 +
 // bw - 1 of the triangle part (see the file comment).  Whole block.
-__device__ inline void tc_apply_chunk(const TcChunk& ch, int kk0, int bw, int p, const float* Tm, TcState& tc) {
+__device__ inline void tc_apply_chunk(const TcChunk& ch, int kk0, int bw, int p, const float* Tm,
+                                      TcState& tc) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q4 = warp & 3, half = warp >> 2;
     const uint32_t lanes = (uint32_t)(32 * q4) << 16;
     const int w = ch.w;
     const int KP = (p + 7) & ~7;
-    const int NP = (w + 15) & ~15;
+    const int NR = (p + 15) & ~15;   // rows of the second product (its N)
     const int* abort = reinterpret_cast<const int*>(tc.smem + TcSmem::ABORT);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(tc.smem + TcSmem::MBAR);
     // Thread-column c = 32 q4 + lane (the same column for both warp halves): its block column.
@@ -449,52 +450,42 @@ __device__ inline void tc_apply_chunk(const TcChunk& ch, int kk0, int bw, int p,
     tc::fence_proxy_async_smem();
     tc::fence_before();
     __syncthreads();
-    // 4. D2 = V W2 (M = 128 rows r, N = NP columns, K = 32).
+    // 4. D2^T = W2^T V^T (M = 128 chunk columns c, N = NR rows r, K = 32): lane c, column r --
+    //    the layout of Xb^T in TMEM, so step 5 updates a column from its own TMEM lane.
     if (tid == 0 && !*abort) {
         tc::fence_after();
-        const uint32_t id = tc::idesc_tf32(128, NP);
-        const uint64_t ah = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::A2H), 128, 0);
-        const uint64_t al = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::A2L), 128, 0);
-        const uint64_t bh = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::B2H), 128, 0);
-        const uint64_t bl = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::B2L), 128, 0);
+        const uint32_t id = tc::idesc_tf32(128, NR);
+        const uint64_t wh = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::B2H), 128, 0);
+        const uint64_t wl = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::B2L), 128, 0);
+        const uint64_t vh = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::A2H), 128, 0);
+        const uint64_t vl = tc::tile_desc(tc::smem_u32(tc.smem + TcSmem::A2L), 128, 0);
         const uint32_t d2 = tc.tmem + TM_D2;
         for (int s = 0; s < PB / 8; ++s) {
             const uint64_t st = (uint64_t)((32 * 128 * s) >> 4);
-            tc::mma_ss(d2, al + st, bh + st, id, s > 0 ? 1u : 0u);
-            tc::mma_ss(d2, ah + st, bl + st, id, 1u);
-            tc::mma_ss(d2, ah + st, bh + st, id, 1u);
+            tc::mma_ss(d2, wh + st, vl + st, id, s > 0 ? 1u : 0u);
+            tc::mma_ss(d2, wl + st, vh + st, id, 1u);
+            tc::mma_ss(d2, wh + st, vh + st, id, 1u);
         }
         tc::commit(mbar);
     }
     tc_wait(tc);
-    // 5. Xb -= D2.  Warp (q4, half) owns rows 32 q4 .. 32 q4 + 31 and the columns of its half;
-    //    each 32 x 32 piece read from TMEM (thread = row) is transposed through the free B2 tile
-    //    (XOR swizzle, no bank conflicts) so that the read-modify-write of Xb runs along rows,
-    //    lane = column.
+    // 5. Xb = (Xb^T hi + lo) - D2^T, from this column's TMEM lane (rows 64 half .. + 63 in two
+    //    32-row pieces); the stores of a warp run along a row, lane = column.
     {
-        float* S = reinterpret_cast<float*>(tc.smem + TcSmem::B2H) + warp * 1024;   // 32 x 32
-        const int cl0 = half * 64;
-        for (int cb = cl0; cb < cl0 + 64 && cb < NP; cb += 32) {
-            float v[32];
-            tc::tmem_ld32(tc.tmem + lanes + TM_D2 + (uint32_t)cb, v);
+        float* base = live ? ch.b[sg].bot + cc : nullptr;
+        const int64_t ldb = live ? ch.b[sg].ldb : 0;
+        for (int piece = 0; piece < 2; ++piece) {
+            const int r0 = 64 * half + 32 * piece;
+            if (r0 >= KP) break;   // uniform over the warp
+            float x[32], t[32];
+            tc::tmem_ld32(tc.tmem + lanes + TM_A1H + (uint32_t)r0, x);
+            tc::tmem_ld32(tc.tmem + lanes + TM_A1L + (uint32_t)r0, t);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) S[lane * 32 + (j ^ lane)] = v[j];
-            __syncwarp();
-            // lane = chunk column cb + lane: its block and in-block column
-            const int cj = cb + lane;
-            const bool cl = cj < w;
-            const int sj = cl ? tc_seg(ch, cj) : 0;
-            float* base = cl ? ch.b[sj].bot + ch.c0[sj] + (cj - ch.off[sj]) : nullptr;
-            const int64_t ldb = cl ? ch.b[sj].ldb : 0;
-            const int r0 = 32 * q4;
-            float xo[32];
+            for (int rr = 0; rr < 32; ++rr) x[rr] += t[rr];
+            tc::tmem_ld32(tc.tmem + lanes + TM_D2 + (uint32_t)r0, t);
 #pragma unroll
             for (int rr = 0; rr < 32; ++rr)
-                xo[rr] = (cl && r0 + rr < p) ? base[(int64_t)(r0 + rr) * ldb] : 0.f;
-#pragma unroll
-            for (int rr = 0; rr < 32; ++rr)
-                if (cl && r0 + rr < p) base[(int64_t)(r0 + rr) * ldb] = xo[rr] - S[rr * 32 + (lane ^ rr)];
-            __syncwarp();
+                if (live && r0 + rr < p) base[(int64_t)(r0 + rr) * ldb] = x[rr] - t[rr];
         }
     }
     tc::fence_before();
