@@ -1509,9 +1509,32 @@ __device__ void sel_tc_store(int M, int N, int NP, FS store, SelTc& st) {
     tc::fence_after();
 }
 
+// C = A B for M x N outputs and K terms as 128-row by 256-column tiles, each one product in
+// TMEM and one epilogue; store(i, j, v) receives every output.  upper: A is upper triangular
+// (A(i, kk) = 0 for kk < i), so row tile r0 starts its K range at r0.  The tiles of a row tile
+// are stored before the next row tile is computed; with `upper` a product may therefore
+// overwrite its B operand in place row tile by row tile (row tile r0 reads rows >= r0 of B).
+template <typename FA, typename FB, typename FS>
+__device__ void sel_tc_product(int M, int N, int K, FA A, FB B, FS store, SelTc& st, bool upper) {
+    for (int r0 = 0; r0 < M; r0 += 128) {
+        const int klo = upper ? r0 : 0;
+        for (int c0 = 0; c0 < N; c0 += 256) {
+            const int nw = (N - c0) < 256 ? (N - c0) : 256;
+            const int NP = (nw + 15) & ~15;
+            sel_tc_gemm(K - klo, NP, [&](int i, int kk) { return A(r0 + i, klo + kk); },
+                        [&](int kk, int j) { return B(klo + kk, c0 + j); }, st);
+            sel_tc_store((M - r0) < 128 ? (M - r0) : 128, nw, NP,
+                         [&](int i, int j, float v) { store(r0 + i, c0 + j, v); }, st);
+        }
+    }
+}
+
 // Row q of level `level` with the products on the tensor cores (see selinv_row for the data).
+// Above PMAX (ri_global != nullptr) Rd^{-1} and M live in this block's global slice and every
+// product is tiled by sel_tc_product.
 __device__ inline void selinv_row_tc(int n, int64_t k, int level, int64_t q, const float* __restrict__ R,
-                                     float* Sx, double* Sd, unsigned long long* bad, SelTc& st) {
+                                     float* Sx, double* Sd, unsigned long long* bad, SelTc& st,
+                                     float* ri_global = nullptr) {
     const int tid = threadIdx.x;
     const int64_t nn = (int64_t)n * n;
     const int64_t c = ((2 * q + 1) << level) - 1;
@@ -1526,9 +1549,11 @@ __device__ inline void selinv_row_tc(int n, int64_t k, int level, int64_t q, con
     const float* Rr = Rc + 2 * nn;
     float* Sl = Sx + c * 2 * nn;
     float* Sr = Sl + nn;
-    float* Ri = reinterpret_cast<float*>(st.smem + SelTcSmem::RI);
+    float* Ri = ri_global ? ri_global : reinterpret_cast<float*>(st.smem + SelTcSmem::RI);
     double* slot = Sd + c * nn;
-    float* Mx = reinterpret_cast<float*>(slot) + nn;   // M in the second half of the FP64 slot
+    // M: in the second half of the FP64 slot (n <= PMAX; S_cc is stored only after all of M is
+    // read), else after Rd^{-1} in the global slice
+    float* Mx = ri_global ? ri_global + nn : reinterpret_cast<float*>(slot) + nn;
 
     // Ri = Rd^{-1} (upper triangular), one thread per column.
     for (int64_t e = tid; e < nn; e += NTH) Ri[e] = 0.f;
@@ -1567,20 +1592,19 @@ __device__ inline void selinv_row_tc(int n, int64_t k, int level, int64_t q, con
     auto put = [&](int i, int j, float v) {
         if (j < n) Sl[(int64_t)i * n + j] = v; else Sr[(int64_t)i * n + j - n] = v;
     };
-    const int N2 = 2 * n, NP2 = (N2 + 15) & ~15, NP1 = (n + 15) & ~15;
+    const int N2 = 2 * n;
     // P = [Rl | Rr] S_II -> [Sl | Sr]
-    sel_tc_gemm(N2, NP2, Aop, Sii, st);
-    sel_tc_store(n, N2, NP2, put, st);
-    // [Sl | Sr] = -Ri P
-    sel_tc_gemm(n, NP2, [&](int i, int p) { return (i < n && p < n) ? Ri[i * n + p] : 0.f; }, SlSr, st);
-    sel_tc_store(n, N2, NP2, [&](int i, int j, float v) { put(i, j, -v); }, st);
+    sel_tc_product(n, N2, N2, Aop, Sii, put, st, false);
+    // [Sl | Sr] = -Ri P, in place (Ri upper triangular)
+    sel_tc_product(n, N2, n, [&](int i, int p) { return (i < n && p < n) ? Ri[i * n + p] : 0.f; }, SlSr,
+                   [&](int i, int j, float v) { put(i, j, -v); }, st, true);
     // M = Ri - [Sl | Sr] [Rl | Rr]^T
-    sel_tc_gemm(N2, NP1, SlSr, [&](int p, int j) { return Aop(j, p); }, st);
-    sel_tc_store(n, n, NP1, [&](int i, int j, float v) { Mx[(int64_t)i * n + j] = Ri[i * n + j] - v; }, st);
-    // S_cc = M Ri^T (doubles into the slot; all of M is in TMEM-side products before any store)
-    sel_tc_gemm(n, NP1, [&](int i, int p) { return (i < n && p < n) ? Mx[(int64_t)i * n + p] : 0.f; },
-                [&](int p, int j) { return (p < n && j < n) ? Ri[j * n + p] : 0.f; }, st);
-    sel_tc_store(n, n, NP1, [&](int i, int j, float v) { slot[(int64_t)i * n + j] = (double)v; }, st);
+    sel_tc_product(n, n, N2, SlSr, [&](int p, int j) { return Aop(j, p); },
+                   [&](int i, int j, float v) { Mx[(int64_t)i * n + j] = Ri[i * n + j] - v; }, st, false);
+    // S_cc = M Ri^T (doubles into the slot; all of M is read before S_cc is stored)
+    sel_tc_product(n, n, n, [&](int i, int p) { return (i < n && p < n) ? Mx[(int64_t)i * n + p] : 0.f; },
+                   [&](int p, int j) { return (p < n && j < n) ? Ri[j * n + p] : 0.f; },
+                   [&](int i, int j, float v) { slot[(int64_t)i * n + j] = (double)v; }, st, false);
     // symmetrise, check the diagonal
     for (int64_t e = tid; e < nn; e += NTH) {
         const int r = (int)(e / n), cc = (int)(e - (int64_t)r * n);
