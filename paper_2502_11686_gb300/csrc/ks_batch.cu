@@ -70,6 +70,8 @@ int floor_log2(int64_t k) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+constexpr int TUNE_FAMILY = 64;   // tuned value = family * TUNE_FAMILY + blocks per SM
+
 void load_tuning(ks_ctx* ctx) {
     if (ctx->tune_loaded) return;
     ctx->tune_loaded = true;
@@ -357,8 +359,10 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
     KS_CUDA(ctx, cudaMemsetAsync(ws + res_begin, 0, res_end - res_begin, st));
 
     // ---- one launch of the sequence ----
+    // A tuned value is family * TUNE_FAMILY + blocks per SM (family: the level kernel of a
+    // generic group, 0 = register-column, 1 = column owner; see launch_batch_generic).
     auto grid_of = [&](const Group& g, int op) -> unsigned {
-        const int tuned = ctx->tuned.count(g.sig(fp32)) ? ctx->tuned[g.sig(fp32)] : 0;
+        const int tuned = ctx->tuned.count(g.sig(fp32)) ? ctx->tuned[g.sig(fp32)] % TUNE_FAMILY : 0;
         int bps;
         if (g.small) bps = (op == B_LEVEL || op == B_SELINV) ? (tuned ? tuned : 8) : 16;
         else if (op == B_WHITEN || op == B_LEVEL || op == B_SELINV) bps = (op == B_WHITEN) ? 8 : (tuned ? tuned : 8);
@@ -366,11 +370,17 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
         else bps = 8;
         return (unsigned)(nsm * bps);
     };
-    auto issue = [&](const Launch& l, unsigned grid) -> cudaError_t {
+    auto family_of = [&](const Group& g) -> int {
+        return ctx->tuned.count(g.sig(fp32)) ? ctx->tuned[g.sig(fp32)] / TUNE_FAMILY : 0;
+    };
+    auto issue_f = [&](const Launch& l, unsigned grid, int family) -> cudaError_t {
         const Group& g = groups[l.group];
         const BatchWork* wk = (const BatchWork*)(meta + l.work_off);
         if (g.small) return g.sops->batch(l.op, wk, fp32, grid, st);
-        return launch_batch_generic(l.op, g.n, g.mmax, wk, fp32, grid, st);
+        return launch_batch_generic(l.op, g.n, g.mmax, wk, fp32, grid, st, family);
+    };
+    auto issue = [&](const Launch& l, unsigned grid) -> cudaError_t {
+        return issue_f(l, grid, family_of(groups[l.group]));
     };
 
     // Batch shape: groups, their deepest levels, covariances, precision, capacity and grids.
@@ -418,24 +428,29 @@ extern "C" ks_status ks_smooth_batch(ks_ctx* ctx, int nprob, const ks_problem* p
                 use_large(g.n, fp32)) {
                 ctx->tuned[sig] = 2;   // the large-state level kernel works in place: not repeatable
             } else if (l.op == B_LEVEL && l.level == 0 && !ctx->tuned.count(sig)) {
+                // Candidates: the persistent grid (blocks per SM) and, where the state dimension
+                // has a register-column level kernel, that kernel or the column-owner one.
                 static const int cand[] = {1, 2, 4, 8, 16, 32};
+                const int nfam = (!g.small && med_ops(g.n, fp32) != nullptr) ? 2 : 1;
                 float best = 1e30f;
-                int best_bps = 8;
-                for (int bps : cand) {
-                    for (int rep = 0; rep < 2; ++rep) {   // first repetition warms up
-                        KS_CUDA(ctx, cudaEventRecord(e0, st));
-                        KS_CUDA(ctx, issue(l, (unsigned)(nsm * bps)));
-                        KS_CUDA(ctx, cudaEventRecord(e1, st));
-                        KS_CUDA(ctx, cudaEventSynchronize(e1));
-                        float ms = 0.f;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        if (rep == 1 && ms < best) {
-                            best = ms;
-                            best_bps = bps;
+                int best_val = 8;
+                for (int fam = 0; fam < nfam; ++fam) {
+                    for (int bps : cand) {
+                        for (int rep = 0; rep < 2; ++rep) {   // first repetition warms up
+                            KS_CUDA(ctx, cudaEventRecord(e0, st));
+                            KS_CUDA(ctx, issue_f(l, (unsigned)(nsm * bps), fam));
+                            KS_CUDA(ctx, cudaEventRecord(e1, st));
+                            KS_CUDA(ctx, cudaEventSynchronize(e1));
+                            float ms = 0.f;
+                            cudaEventElapsedTime(&ms, e0, e1);
+                            if (rep == 1 && ms < best) {
+                                best = ms;
+                                best_val = fam * TUNE_FAMILY + bps;
+                            }
                         }
                     }
                 }
-                ctx->tuned[sig] = best_bps;
+                ctx->tuned[sig] = best_val;
             }
             KS_CUDA(ctx, issue(l, grid_of(g, l.op)));
         }

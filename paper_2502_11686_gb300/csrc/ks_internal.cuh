@@ -457,8 +457,9 @@ const MedOps* med_ops(int n, bool fp32);
 const MedOps* med_whiten_ops(int n, int mmax, bool fp32);
 
 // Batched column-owner launches (classes with n > 8 or some m_i > n).
+// family (levels of n with a register-column kernel): 0 = register-column, 1 = column owner.
 cudaError_t launch_batch_generic(int op, int n, int mmax, const BatchWork* wk, bool fp32,
-                                 unsigned grid, cudaStream_t st);
+                                 unsigned grid, cudaStream_t st, int family = 0);
 const SmallOps* small_ops(int n);
 constexpr int SMALL_NMAX = 8;
 

@@ -425,14 +425,14 @@ static cudaError_t batch_generic_t(int op, int n, int mmax, const BatchWork* wk,
 }
 
 cudaError_t launch_batch_generic(int op, int n, int mmax, const BatchWork* wk, bool fp32,
-                                 unsigned grid, cudaStream_t st) {
+                                 unsigned grid, cudaStream_t st, int family) {
     if (use_large(n, fp32) && (op == B_WHITEN || op == B_LEVEL || op == B_SELINV))
         return launch_batch_large(op, n, wk, fp32, grid, st);
     if (op == B_WHITEN)
         if (const MedOps* m = med_whiten_ops(n, mmax, fp32)) return m->batch_whiten(wk, fp32, grid, st);
     if (op == B_WHITEN && !generic_whiten_fits(n, mmax))
         return launch_batch_large(op, n, wk, fp32, grid, st);
-    if (op == B_LEVEL)
+    if (op == B_LEVEL && family == 0)
         if (const MedOps* m = med_ops(n, fp32)) return m->batch_level(wk, fp32, grid, st);
     if (n <= 64)
         return fp32 ? batch_generic_t<float, 2>(op, n, mmax, wk, grid, st)

@@ -136,3 +136,54 @@ def test_batch_reports_failing_problem(sm64):
     assert st == native.KS_ERR_NOT_SPD
     assert sts == [native.KS_OK, native.KS_ERR_NOT_SPD] and infos[1] == 7
     assert rel(to_np(batch[0]["u_out"]), oracle.smooth(good, covariances=False)["u"]) < 1e-10
+
+
+FAMILY = 64   # tuned value in the tune cache = family * FAMILY + blocks per SM
+
+
+def _batch_with_cache(problems, path):
+    o = native.ks_default_options()
+    o.precision = native.KS_FP64
+    cache = str(path).encode()
+    o.tune_cache = cache
+    ctx = native.ks_create(o)
+    try:
+        batch = as_batch(problems)
+        native.ks_smooth_batch(ctx, batch)
+        return [(to_np(b["u_out"]).copy(), to_np(b["cov_out"])) for b in batch]
+    finally:
+        native.ks_destroy(ctx)
+
+
+def _register_column_problems():
+    return [(inputs.random_problem(k, n, n, seed=700 + n, with_c=True, f_scale=0.99), True)
+            for k, n in [(257, 12), (129, 16), (96, 32)]]
+
+
+def test_batch_tuner_picks_grid_and_level_kernel(tmp_path):
+    """The first batch of a new group tunes its level launch over the persistent grid and, for
+    state dimensions with a register-column level kernel, over the kernel family; the choice
+    is written to the tune cache as family * 64 + blocks per SM."""
+    problems = _register_column_problems()
+    path = tmp_path / "tune.txt"
+    out = _batch_with_cache(problems, path)
+    for (p, _), (u, cov) in zip(problems, out):
+        ref = oracle.smooth(p, covariances=True)
+        assert rel(u, ref["u"]) < 1e-10 and rel_blocks(cov, ref["cov"]) < 1e-10
+    tuned = dict(line.split() for line in path.read_text().splitlines())
+    for n in (12, 16, 32):
+        v = int(tuned[f"f64:n{n}:g:m{n}"])
+        assert v // FAMILY in (0, 1) and v % FAMILY in (1, 2, 4, 8, 16, 32), (n, v)
+
+
+@pytest.mark.parametrize("family", [0, 1], ids=["register_column", "column_owner"])
+def test_batch_level_kernel_family_from_cache(family, tmp_path):
+    """Either level kernel family, forced through the tune cache, matches the oracle."""
+    problems = _register_column_problems()
+    path = tmp_path / "tune.txt"
+    path.write_text("".join(f"f64:n{n}:g:m{n} {family * FAMILY + 8}\n" for n in (12, 16, 32)))
+    out = _batch_with_cache(problems, path)
+    for (p, _), (u, cov) in zip(problems, out):
+        ref = oracle.smooth(p, covariances=True)
+        assert rel(u, ref["u"]) < 1e-10, (family, p.n)
+        assert rel_blocks(cov, ref["cov"]) < 1e-10, (family, p.n)
