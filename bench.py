@@ -316,12 +316,19 @@ def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, step
     stream = torch.cuda.Stream()
     prec = native.KS_FP64 if precision == "fp64" else native.KS_FP32_REFINE
 
+    # The autotuner's choices (grid and level kernel family per group) go to a tune cache that
+    # every ctx of this record shares, and into the record.
+    import tempfile
+    tune_dir = tempfile.mkdtemp(prefix="ks_tune_")
+    tune_path = os.path.join(tune_dir, "tune.txt").encode()
+
     def make_ctx(profile):
         o = native.ks_default_options()
         o.precision = prec
         o.stream = stream.cuda_stream
         o.profile = 1 if profile else 0
         o.sync = 0
+        o.tune_cache = tune_path
         return native.ks_create(o)
 
     log(f"batched record: drawing {nprob} problems ({total_k} states) on the device")
@@ -413,6 +420,9 @@ def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, step
     top = max(flops, key=lambda ph: phase_ms.get(ph, 0.0))
     fp64_phase = precision == "fp64" or top in ("whiten", "refine")
     roof = alu_roofline(f"{top} phase (batched launches)", flops[top], phase_ms[top], fp64_phase)
+    tuned = read_tuning(tune_path.decode())
+    import shutil
+    shutil.rmtree(tune_dir, ignore_errors=True)
     cpu = None
     if pool is not None:
         log(f"batched record: CPU baseline on {cores} host cores")
@@ -426,9 +436,28 @@ def batch_record(args, nprob, precision, pool=None, cores=1, want_e2e=True, step
                    "inputs": "drawn on the device per problem seed (ks_generate_steps)",
                    "l2": f"inputs ({in_bytes / 1e9:.1f} GB) larger than L2, no flush"},
         "roofline": roof, "phase_ms_per_step": phase_ms, "cpu_baseline": cpu, "e2e": e2e,
+        "tuned": tuned,
         "gpu_launches": prof_graph["launches"] // max(1, steps + warmup) * steps,
         "clocks": clk.summary(),
     }
+
+
+def read_tuning(path):
+    """The batched autotuner's choices from its tune cache: per group signature (precision,
+    state dimension, s = small-state path or g = block kernels, largest observation count), the
+    level kernel family (0: the default kernel for that dimension -- register-column where one
+    is compiled; 1: column owner) and the persistent grid in blocks per SM (cache value =
+    family * 64 + blocks per SM)."""
+    out = {}
+    try:
+        with open(path) as fh:
+            for line in fh:
+                sig, v = line.split()
+                v = int(v)
+                out[sig] = {"level_kernel_family": v // 64, "blocks_per_sm": v % 64}
+    except OSError:
+        pass
+    return out
 
 
 def batch_arm(args):
