@@ -88,7 +88,9 @@ typedef struct {
     int profile;        /* 1 = time every phase with CUDA events on the ctx's stream */
     const char *tune_cache; /* file where ks_smooth_batch keeps its tuned launch shapes (read at
                                the first batch, rewritten after tuning); NULL = keep them in the
-                               ctx only */
+                               ctx only.  One line per problem group: its signature, then
+                               family * 64 + blocks per SM, family 0 = the default level kernel
+                               of that state dimension, 1 = the column-owner kernel */
 } ks_options;
 
 /* Phases reported by ks_profile_read (indices of phase_ms / phase_launches). */
